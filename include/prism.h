@@ -1,0 +1,191 @@
+/*
+ * prism.h -- C-ABI of the GB300 (sm_103a) PRISM fitting library.
+ *
+ * PRISM (Abouagour, Shah, Garyfallidis, "PRISM: Differentiable Analysis-by-
+ * Synthesis for Fixel Recovery in Diffusion MRI") fits, per voxel x of a brain
+ * mask and measurement n (b-value b_n, unit gradient g_n), the forward model
+ *
+ *   S(x,n)    = S0 (f_csf E_csf + f_gm E_gm + sum_k f_wm,k E_wm,k + f_res E_res)   Sec. 2.2, Eq. 2
+ *   E_iso     = exp(-b D_iso), D = 3.0 / 0.9 / 0.2 x 1e-3 mm^2/s                   Sec. 2.2, Eq. 3
+ *   E_wm,k    = f_in e^{-b D_par c^2} + (1-f_in) e^{-b (D_par c^2 + D_perp (1-c^2))},
+ *               c = d_k . g_n, D_par = 1.7e-3, D_perp = 0.4e-3                     Sec. 2.2, Eq. 4
+ *   y_hat     = exp(alpha_n) B(x) S(x,n) + beta_n, B = exp(trilinear(b_lr 8^3))    Sec. 2.3, Eq. 5
+ *
+ * to b0-normalised data y (Sec. 2.5) by minimising the MSE (Eq. 7) or the
+ * Rician NLL with learned sigma = exp(sigma_log) (Eq. 8), plus the priors of
+ * Sec. 2.4, with Adam (the Table 2 comparator). Each iteration computes the
+ * objective, its exact gradient (hand-written adjoint) and one Adam update of
+ * every parameter.
+ *
+ * Conventions
+ *  - Every function returns PRISM_OK (0) or a prism_status code; the message
+ *    of the last failure on the calling thread is prism_last_error(). No C++
+ *    exception crosses this boundary.
+ *  - `stream` arguments are cudaStream_t values passed as void* (NULL = the
+ *    legacy default stream). Work is enqueued on that stream; functions that
+ *    return host data synchronise it. Asynchronous device errors surface at the
+ *    next synchronising call (prism_sync, prism_get_*).
+ *  - A voxel index v runs over the masked voxels of volume 0 in C order of
+ *    (x, y, z), then volume 1, and so on ("mask order"). V = total voxels.
+ *  - Raw per-voxel parameters, Q = 4K + 5 per voxel, in this order:
+ *      [0]            s        S0 = softplus(s)
+ *      [1 .. K+3]     logits   fractions = softmax over [csf, gm, wm_1..wm_K, res]
+ *      [K+4 .. 4K+3]  v_k      3 components per fiber, d_k = v_k / max(|v_k|, 1e-12)
+ *      [4K+4]         u        f_intra = sigmoid(u)
+ *  - The handle owns every device buffer it allocates; caller buffers are only
+ *    read during the call that receives them (init copies what it needs).
+ *  - Handles are not thread-safe; distinct handles may be used concurrently.
+ */
+#ifndef PRISM_H
+#define PRISM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum prism_status {
+  PRISM_OK = 0,
+  PRISM_E_INVALID_ARG = 1, /* NULL pointer, option out of range */
+  PRISM_E_SHAPE = 2,       /* inconsistent sizes, empty mask, no b=0 measurement */
+  PRISM_E_CUDA = 3,        /* a CUDA runtime call failed */
+  PRISM_E_OOM = 4,         /* device allocation failed */
+  PRISM_E_NONFINITE = 5,   /* non-finite input signal / b0, or the objective became NaN/Inf */
+  PRISM_E_TIMEOUT = 6,     /* a bounded device-side wait gave up (status word set by a kernel) */
+  PRISM_E_STATE = 7        /* call out of order (e.g. backward without forward), bad checkpoint */
+} prism_status;
+
+enum { PRISM_LOSS_MSE = 0, PRISM_LOSS_NLL = 1 };
+enum { PRISM_MEM_HOST = 0, PRISM_MEM_DEVICE = 1 };
+enum { PRISM_MAX_K = 5, PRISM_BIAS_GRID = 8 };
+
+/* One volume = one calibration / noise group (Sec. 2.3: b_lr, alpha_n, beta_n, sigma). */
+typedef struct prism_volume {
+  int32_t nx, ny, nz;     /* grid size, each >= 1 */
+  int32_t n_meas;         /* N >= 1; at least one b <= 50 s/mm^2 (used for b0 normalisation) */
+  int32_t mem;            /* PRISM_MEM_HOST or PRISM_MEM_DEVICE: where `signal` and `init` live */
+  int32_t reserved;
+  const uint8_t* mask;    /* HOST [nx][ny][nz], C order, nonzero = inside the brain mask */
+  const float* signal;    /* [V_vol][N] raw magnitudes of the masked voxels in mask order */
+  const float* bvals;     /* HOST [N] b-values, s/mm^2 (>= 0) */
+  const float* bvecs;     /* HOST [N][3] gradient directions; rows with b > 50 must be unit (|g|-1| < 1e-3) */
+  const float* init;      /* [V_vol][Q] raw initial parameters, or NULL for the seeded default */
+} prism_volume;
+
+typedef struct prism_options {
+  int32_t K;              /* fibers per voxel, 1..5 */
+  int32_t loss;           /* PRISM_LOSS_MSE (Eq. 7) or PRISM_LOSS_NLL (Eq. 8) */
+  int32_t calibration;    /* 1: learn bias field + per-measurement affine (Sec. 2.3) */
+  int32_t patch_dim;      /* spatial patch edge, 1..64; neighbour priors stay inside a patch */
+  float lam_rep;          /* direction repulsion weight (Sec. 2.4), 0.01 */
+  float lam_sparse;       /* L1 on minor fiber fractions, 0.02 */
+  float tau;              /* minor-fraction threshold, 0.15 */
+  float lam_sp;           /* Huber-Laplacian fraction smoothness (Eq. 6), 0 = off (paper default 0.01) */
+  float huber_delta;      /* Huber transition, 0.05 */
+  float lam_dir;          /* directional continuity, 0 = off (paper 0.005) */
+  float w_alpha, w_beta, w_blr, w_tv, tv_eps; /* calibration regularisers: 1e-3 each, eps 1e-6 */
+  float sigma_init;       /* sigma start when a volume has < 2 b=0 measurements, 0.05 */
+  float lr, beta1, beta2, eps; /* Adam: 1e-2, 0.9, 0.999, 1e-8 */
+  int32_t fused;          /* 1: persistent fused iteration kernel; 0: plain unfused per-patch launches */
+  int32_t use_graph;      /* 1: replay the fused iteration from a CUDA graph */
+  int32_t threads_per_voxel; /* 1, 4 or 16 (measurements split across lanes); 0 = automatic */
+  int32_t cta_threads;    /* 128 or 256; 0 = automatic */
+  int32_t autotune;       /* 1: time the candidate tile shapes at init and keep the fastest */
+  int32_t seed;           /* seed of the default initialisation (init == NULL) */
+  int32_t reserved[4];
+} prism_options;
+
+/* Fills `opt` with the paper's defaults (MSE, K = 3, no calibration, repulsion + sparsity). */
+void prism_default_options(prism_options* opt);
+
+typedef struct prism_handle prism_handle;
+
+/*
+ * Validates the volumes, b0-normalises the signal (Sec. 2.5), splits each mask
+ * into patch_dim^3 patches and voxel tiles, packs the data for the kernels,
+ * builds the per-measurement tables, and initialises parameters, Adam state and
+ * (if requested) the CUDA graph. Allocates all device memory the fit needs.
+ * Errors: E_INVALID_ARG, E_SHAPE (sizes, empty mask, no b=0), E_NONFINITE
+ * (non-finite signal or non-positive b0 mean), E_OOM, E_CUDA.
+ */
+int prism_fit_init(const prism_volume* vols, int32_t n_vols, const prism_options* opt,
+                   void* stream, prism_handle** out);
+
+/* Enqueues n_iters >= 0 iterations (objective, gradient, Adam update). Asynchronous. */
+int prism_step(prism_handle* h, int32_t n_iters, void* stream);
+
+/* Synchronises `stream` and reports any device-side status (E_TIMEOUT, E_NONFINITE) or CUDA error. */
+int prism_sync(prism_handle* h, void* stream);
+
+/* Sizes: total voxels V, groups, Q, total packed group-parameter floats, iterations done. */
+int prism_info(const prism_handle* h, int64_t* n_vox, int32_t* n_groups, int32_t* q,
+               int64_t* n_group_params, int64_t* iterations);
+
+/* Raw parameters [V][Q] in mask order, to/from host or device memory (per `mem`). */
+int prism_get_params(prism_handle* h, float* out, int32_t mem, void* stream);
+int prism_set_params(prism_handle* h, const float* in, int32_t mem, void* stream);
+
+/*
+ * Packed group parameters. Group g occupies [off[4g], off[4g+4]) of the packed
+ * float array: sigma_log at off[4g], alpha[N_g] at off[4g+1], beta[N_g] at
+ * off[4g+2], b_lr[8][8][8] (C order) at off[4g+3]; off[4G] = total. `off` is a
+ * HOST int64 array of 4G+1 entries.
+ */
+int prism_group_layout(const prism_handle* h, int64_t* off);
+int prism_get_groups(prism_handle* h, float* out, int32_t mem, void* stream);
+int prism_set_groups(prism_handle* h, const float* in, int32_t mem, void* stream);
+
+/*
+ * Objective per group J_g (data term + priors + calibration regularisers,
+ * Sec. 2.5) evaluated at the parameters before the most recent update, as
+ * double. `hist` (HOST, may be NULL) receives up to `max_iters` x G values of
+ * the most recent iterations, oldest first; `*n_written` the iteration count.
+ */
+int prism_get_loss(prism_handle* h, double* loss, double* hist, int32_t max_iters,
+                   int32_t* n_written);
+
+/*
+ * Forward evaluation at `theta` (DEVICE [V][Q], or NULL = current parameters)
+ * and `groups` (DEVICE packed, or NULL = current): synthesis, calibration and
+ * data term, plus the prior values. Writes y_hat (DEVICE, NULL to skip; group g
+ * at offset sum_{g'<g} V_g' N_g', rows [V_g][N_g] in mask order) and J_g
+ * (DEVICE double [G]). Keeps the residual derivative dL/dy_hat (V x N, not the
+ * V x N x K compartment terms) for prism_backward.
+ */
+int prism_forward(prism_handle* h, const float* theta, const float* groups, float* yhat,
+                  double* loss, void* stream);
+
+/*
+ * Gradient of the objective at the point of the last prism_forward: recomputes
+ * the compartment exponentials, then the adjoint of synthesis, calibration,
+ * data term and priors. grad_theta DEVICE [V][Q]; grad_groups DEVICE packed
+ * (NULL to skip). E_STATE without a preceding forward.
+ */
+int prism_backward(prism_handle* h, float* grad_theta, float* grad_groups, void* stream);
+
+/* Checkpoint: parameters, Adam moments, step counter and group state as one blob. */
+int prism_state_size(const prism_handle* h, int64_t* bytes);
+int prism_get_state(prism_handle* h, void* host_buf, int64_t bytes, void* stream);
+int prism_set_state(prism_handle* h, const void* host_buf, int64_t bytes, void* stream);
+
+/*
+ * One-call fit: init + n_iters iterations + readout + destroy. params_out
+ * [V][Q] and loss_out [G] (double) live in `out_mem` memory (either may be
+ * NULL). Synchronous.
+ */
+int prism_fit(const prism_volume* vols, int32_t n_vols, const prism_options* opt,
+              int32_t n_iters, float* params_out, double* loss_out, int32_t out_mem,
+              void* stream);
+
+/* Frees every device buffer and graph of the handle. NULL is a no-op. */
+void prism_fit_destroy(prism_handle* h);
+
+/* Message of the last failure on this thread ("" if none). Valid until the next call. */
+const char* prism_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PRISM_H */

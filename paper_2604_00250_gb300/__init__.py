@@ -1,0 +1,314 @@
+"""GB300 (sm_103a) implementation of the PRISM analysis-by-synthesis fit.
+
+Python binding of the C-ABI library (include/prism.h). Every step of the fit runs
+in the library's CUDA kernels; this module only marshals arguments. PyTorch
+provides device memory and streams.
+
+    import paper_2604_00250_gb300 as prism
+    f = prism.Fitter(volumes, prism.options(K=3, loss="mse"))
+    f.step(200)
+    theta = f.params()           # [V, 4K+5] raw parameters, mask order
+
+`volumes` are objects with `mask` (uint8 [nx, ny, nz]), `signal` ([V, N] float32,
+numpy for host memory or a CUDA tensor), `bvals` [N] and `bvecs` [N, 3].
+"""
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import PrismError, MEM_HOST, MEM_DEVICE, LOSS_MSE, LOSS_NLL
+
+__all__ = ["options", "Fitter", "fit", "PrismLoss", "PrismError", "library_path"]
+
+
+def library_path():
+    return _lib.LIB_PATH
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def options(**kw):
+    """prism_options with the paper's defaults, overridden by keyword (loss="mse"|"nll")."""
+    lib = _lib.load()
+    o = _lib.Options()
+    lib.prism_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "loss" and isinstance(v, str):
+            v = {"mse": LOSS_MSE, "nll": LOSS_NLL}[v.lower()]
+        if isinstance(v, bool):
+            v = int(v)
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k!r}")
+        setattr(o, k, v)
+    return o
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    if stream is None:
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        return ctypes.c_void_p(0)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _host_f32(a, shape=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    if shape is not None and a.shape != tuple(shape):
+        raise ValueError(f"expected shape {shape}, got {a.shape}")
+    return a
+
+
+def _volume_struct(vol, keep):
+    torch = _torch()
+    mask = np.ascontiguousarray(np.asarray(vol.mask).astype(np.uint8))
+    if mask.ndim != 3:
+        raise ValueError("mask must be 3-D")
+    bvals = _host_f32(vol.bvals)
+    N = int(bvals.shape[0])
+    bvecs = _host_f32(vol.bvecs, (N, 3))
+    sig = vol.signal
+    init = getattr(vol, "init", None)
+    V = int(mask.astype(bool).sum())
+    if isinstance(sig, torch.Tensor) and sig.is_cuda:
+        mem = MEM_DEVICE
+        sig = sig.detach().to(torch.float32).contiguous()
+        if tuple(sig.shape) != (V, N):
+            raise ValueError(f"signal must be [V={V}, N={N}], got {tuple(sig.shape)}")
+        sp = sig.data_ptr()
+        ip = None
+        if init is not None:
+            init = torch.as_tensor(init, device=sig.device, dtype=torch.float32).contiguous()
+            ip = init.data_ptr()
+    else:
+        mem = MEM_HOST
+        if isinstance(sig, torch.Tensor):
+            sig = sig.detach().cpu().numpy()
+        sig = _host_f32(sig, (V, N))
+        sp = sig.ctypes.data
+        ip = None
+        if init is not None:
+            if isinstance(init, torch.Tensor):
+                init = init.detach().cpu().numpy()
+            init = _host_f32(init)
+            ip = init.ctypes.data
+    keep.extend([mask, bvals, bvecs, sig, init])
+    nx, ny, nz = mask.shape
+    return _lib.Volume(nx, ny, nz, N, mem, 0, mask.ctypes.data, sp, bvals.ctypes.data, bvecs.ctypes.data, ip)
+
+
+def _volumes_array(volumes, keep):
+    if not isinstance(volumes, (list, tuple)):
+        volumes = [volumes]
+    arr = (_lib.Volume * len(volumes))()
+    for i, v in enumerate(volumes):
+        arr[i] = _volume_struct(v, keep)
+    return arr, len(volumes)
+
+
+class Fitter:
+    """One PRISM fit (a handle of the C library) over a batch of volumes."""
+
+    def __init__(self, volumes, opts=None, stream=None, **kw):
+        lib = _lib.load()
+        self._lib = lib
+        self.opts = opts if opts is not None else options(**kw)
+        keep = []
+        arr, n = _volumes_array(volumes, keep)
+        h = ctypes.c_void_p()
+        _lib.check(lib.prism_fit_init(arr, n, ctypes.byref(self.opts), _stream_ptr(stream), ctypes.byref(h)))
+        self._h = h
+        V, G, Q, GP, it = (ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64(),
+                           ctypes.c_int64())
+        _lib.check(lib.prism_info(h, ctypes.byref(V), ctypes.byref(G), ctypes.byref(Q), ctypes.byref(GP),
+                                  ctypes.byref(it)))
+        self.n_vox, self.n_groups, self.Q, self.n_group_params = V.value, G.value, Q.value, GP.value
+        self.K = int(self.opts.K)
+        vols = volumes if isinstance(volumes, (list, tuple)) else [volumes]
+        self.n_meas = [int(np.asarray(v.bvals).shape[0]) for v in vols]
+        self.yhat_len = sum(int(np.asarray(v.mask).astype(bool).sum()) * n for v, n in zip(vols, self.n_meas))
+
+    # -- lifecycle -----------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.prism_fit_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- iterations ------------------------------------------------------------
+    def step(self, n=1, stream=None):
+        _lib.check(self._lib.prism_step(self._h, int(n), _stream_ptr(stream)))
+
+    def sync(self, stream=None):
+        _lib.check(self._lib.prism_sync(self._h, _stream_ptr(stream)))
+
+    @property
+    def iterations(self):
+        it = ctypes.c_int64()
+        _lib.check(self._lib.prism_info(self._h, None, None, None, None, ctypes.byref(it)))
+        return it.value
+
+    # -- parameters --------------------------------------------------------------
+    def params(self, stream=None):
+        torch = _torch()
+        out = torch.empty((self.n_vox, self.Q), dtype=torch.float32, device="cuda")
+        _lib.check(self._lib.prism_get_params(self._h, ctypes.c_void_p(out.data_ptr()), MEM_DEVICE,
+                                              _stream_ptr(stream)))
+        return out
+
+    def params_host(self):
+        out = np.empty((self.n_vox, self.Q), dtype=np.float32)
+        _lib.check(self._lib.prism_get_params(self._h, out.ctypes.data, MEM_HOST, _stream_ptr(None)))
+        return out
+
+    def set_params(self, theta, stream=None):
+        torch = _torch()
+        t = torch.as_tensor(theta, dtype=torch.float32, device="cuda").contiguous()
+        if tuple(t.shape) != (self.n_vox, self.Q):
+            raise ValueError("theta must be [V, Q]")
+        _lib.check(self._lib.prism_set_params(self._h, ctypes.c_void_p(t.data_ptr()), MEM_DEVICE,
+                                              _stream_ptr(stream)))
+        torch.cuda.current_stream().synchronize()
+
+    def group_layout(self):
+        off = np.zeros(4 * self.n_groups + 1, dtype=np.int64)
+        _lib.check(self._lib.prism_group_layout(self._h, off.ctypes.data))
+        return off
+
+    def groups(self):
+        out = np.empty(self.n_group_params, dtype=np.float32)
+        _lib.check(self._lib.prism_get_groups(self._h, out.ctypes.data, MEM_HOST, _stream_ptr(None)))
+        return out
+
+    def set_groups(self, packed):
+        a = _host_f32(packed, (self.n_group_params,))
+        _lib.check(self._lib.prism_set_groups(self._h, a.ctypes.data, MEM_HOST, _stream_ptr(None)))
+
+    def group_view(self, packed=None):
+        """Per group: sigma_log, alpha [N], beta [N], b_lr [8, 8, 8] from the packed array."""
+        p = self.groups() if packed is None else np.asarray(packed)
+        off = self.group_layout()
+        out = []
+        for g in range(self.n_groups):
+            a, b, c, d = (int(x) for x in off[4 * g:4 * g + 4])
+            N = self.n_meas[g]
+            out.append(dict(sigma_log=float(p[a]), alpha=p[b:b + N], beta=p[c:c + N],
+                            blr=p[d:d + 512].reshape(8, 8, 8)))
+        return out
+
+    # -- objective -----------------------------------------------------------------
+    def loss(self):
+        out = np.empty(self.n_groups, dtype=np.float64)
+        _lib.check(self._lib.prism_get_loss(self._h, out.ctypes.data, None, 0, None))
+        return out
+
+    def loss_history(self, max_iters=4096):
+        out = np.empty((max_iters, self.n_groups), dtype=np.float64)
+        n = ctypes.c_int32()
+        _lib.check(self._lib.prism_get_loss(self._h, None, out.ctypes.data, max_iters, ctypes.byref(n)))
+        return out[:n.value]
+
+    def forward(self, theta=None, groups=None, want_yhat=False, stream=None):
+        """J per group (CUDA float64 [G]) and optionally y_hat (flat, volume-major rows)."""
+        torch = _torch()
+        loss = torch.empty(self.n_groups, dtype=torch.float64, device="cuda")
+        tp = gp = None
+        if theta is not None:
+            theta = theta.detach().to(torch.float32).contiguous()
+            tp = ctypes.c_void_p(theta.data_ptr())
+        if groups is not None:
+            groups = groups.detach().to(torch.float32).contiguous()
+            gp = ctypes.c_void_p(groups.data_ptr())
+        yhat = None
+        yp = None
+        if want_yhat:
+            yhat = torch.empty(self.yhat_len, dtype=torch.float32, device="cuda")
+            yp = ctypes.c_void_p(yhat.data_ptr())
+        _lib.check(self._lib.prism_forward(self._h, tp, gp, yp, ctypes.c_void_p(loss.data_ptr()),
+                                           _stream_ptr(stream)))
+        return loss, yhat
+
+    def backward(self, stream=None):
+        torch = _torch()
+        gth = torch.empty((self.n_vox, self.Q), dtype=torch.float32, device="cuda")
+        gg = torch.empty(self.n_group_params, dtype=torch.float32, device="cuda")
+        _lib.check(self._lib.prism_backward(self._h, ctypes.c_void_p(gth.data_ptr()),
+                                            ctypes.c_void_p(gg.data_ptr()), _stream_ptr(stream)))
+        return gth, gg
+
+    # -- checkpoint ------------------------------------------------------------------
+    def state(self):
+        n = ctypes.c_int64()
+        _lib.check(self._lib.prism_state_size(self._h, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        _lib.check(self._lib.prism_get_state(self._h, buf, n.value, _stream_ptr(None)))
+        return buf.raw
+
+    def load_state(self, blob):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _lib.check(self._lib.prism_set_state(self._h, buf, len(blob), _stream_ptr(None)))
+
+
+def fit(volumes, opts=None, n_iters=200, stream=None, **kw):
+    """One-call fit (prism_fit): returns (theta [V, Q] numpy float32, J per group numpy float64)."""
+    lib = _lib.load()
+    o = opts if opts is not None else options(**kw)
+    keep = []
+    arr, n = _volumes_array(volumes, keep)
+    V = sum(int(np.asarray(v.mask).astype(bool).sum()) for v in (volumes if isinstance(volumes, (list, tuple)) else [volumes]))
+    theta = np.empty((V, 4 * int(o.K) + 5), dtype=np.float32)
+    loss = np.empty(n, dtype=np.float64)
+    _lib.check(lib.prism_fit(arr, n, ctypes.byref(o), int(n_iters), theta.ctypes.data, loss.ctypes.data, MEM_HOST,
+                             _stream_ptr(stream)))
+    return theta, loss
+
+
+def _make_autograd():
+    torch = _torch()
+
+    class PrismLoss(torch.autograd.Function):
+        """J(theta, groups) = sum_g J_g; forward = synthesis + data term + priors,
+        backward = hand-written adjoint (compartment exponentials recomputed)."""
+
+        @staticmethod
+        def forward(ctx, theta, groups, fitter):
+            loss, _ = fitter.forward(theta, groups)
+            ctx.fitter = fitter
+            return loss.sum()
+
+        @staticmethod
+        def backward(ctx, gout):
+            gth, gg = ctx.fitter.backward()
+            s = gout.to(torch.float32)
+            return gth * s, gg * s, None
+
+    return PrismLoss
+
+
+class _LazyAutograd:
+    _cls = None
+
+    def __getattr__(self, name):
+        if _LazyAutograd._cls is None:
+            _LazyAutograd._cls = _make_autograd()
+        return getattr(_LazyAutograd._cls, name)
+
+
+PrismLoss = _LazyAutograd()

@@ -1,0 +1,1060 @@
+// C-ABI implementation of the PRISM fitting library (host side).
+//
+// Responsibilities: argument validation, the spatial work decomposition (volumes ->
+// patch_dim^3 patches -> voxel tiles), packing of the b0-normalised signal (Sec. 2.5),
+// device workspace, the fused (persistent kernel, CUDA graph) and plain (per-patch
+// launches) iteration drivers, the forward / backward evaluation behind the autograd
+// binding, checkpointing and error reporting.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "prism.h"
+#include "prism_kernels.cuh"
+#include "prism_launch.h"
+
+using namespace prism;
+
+namespace prism {
+const KernelSet& kernels_k1();
+const KernelSet& kernels_k2();
+const KernelSet& kernels_k3();
+const KernelSet& kernels_k4();
+const KernelSet& kernels_k5();
+const KernelSet& kernels_for_k(int K) {
+  switch (K) {
+    case 1: return kernels_k1();
+    case 2: return kernels_k2();
+    case 3: return kernels_k3();
+    case 4: return kernels_k4();
+    default: return kernels_k5();
+  }
+}
+}  // namespace prism
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? PRISM_E_OOM : PRISM_E_CUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+constexpr int kSplitTiles = 64;
+constexpr int kHistLen = 4096;
+constexpr int kGraphUnroll = 16;
+constexpr uint32_t kStateMagic = 0x50524953u;   // "PRIS"
+
+struct PatchRange {
+  int tb, te;
+};
+
+}  // namespace
+
+struct prism_handle {
+  prism_options opt{};
+  int K = 0, Q = 0, XF = 0, TPV = 1, NT = 128, TV = 128;
+  int G = 0, Vpad = 0, ntiles = 0, Nmax = 0, max_e = 0, max_split = 0;
+  int64_t V = 0, GP = 0, iters = 0, ypack_len = 0, tab_rows = 0, ab_len = 0, yhat_len = 0;
+  bool cal = false, nb = false;
+  std::vector<GroupDev> groups;
+  std::vector<Tile> tiles;
+  std::vector<PatchRange> patches;
+  std::vector<int64_t> vox0, gp_layout, yhat_off;
+  std::vector<void*> allocs;
+  // device buffers
+  Tile* d_tiles = nullptr;
+  GroupDev* d_groups = nullptr;
+  float *d_y = nullptr, *d_theta = nullptr, *d_m = nullptr, *d_v = nullptr, *d_xf = nullptr;
+  float *d_hsp = nullptr, *d_lp = nullptr, *d_gU = nullptr, *d_tile_ab = nullptr;
+  float *d_gparams = nullptr, *d_gm = nullptr, *d_gv = nullptr;
+  float *d_yhat = nullptr, *d_r = nullptr, *d_grad = nullptr;
+  int32_t *d_nbr = nullptr, *d_queue = nullptr, *d_done = nullptr, *d_step = nullptr, *d_status = nullptr;
+  float* d_adamc = nullptr;
+  int32_t *d_slot_of_vox = nullptr, *d_vox_of_slot = nullptr, *d_slot_of_grid = nullptr;
+  int32_t *d_split_off = nullptr, *d_counters = nullptr;
+  uint32_t *d_vcoord = nullptr, *d_vflag = nullptr;
+  int64_t* d_row_off = nullptr;
+  MeasRow* d_table = nullptr;
+  double *d_tile_red = nullptr, *d_part2 = nullptr, *d_gred = nullptr, *d_gloss = nullptr;
+  double *d_gprior = nullptr, *d_hist = nullptr;
+  IterArgs ia{};
+  GroupArgs ga{};
+  const KernelSet* ks = nullptr;
+  int fused_grid = 0;
+  size_t fused_smem = 0, adj_smem = 0;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t g1 = nullptr, gU = nullptr;
+  bool forward_done = false;
+
+  template <typename T>
+  int alloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return cuda_fail(e, "cudaMalloc");
+    }
+    allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return PRISM_OK;
+  }
+  ~prism_handle() {
+    if (g1) cudaGraphExecDestroy(g1);
+    if (gU) cudaGraphExecDestroy(gU);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    for (void* p : allocs) cudaFree(p);
+  }
+};
+
+extern "C" void prism_default_options(prism_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->K = 3;
+  o->loss = PRISM_LOSS_MSE;
+  o->calibration = 0;
+  o->patch_dim = 16;
+  o->lam_rep = 0.01f;
+  o->lam_sparse = 0.02f;
+  o->tau = 0.15f;
+  o->lam_sp = 0.f;
+  o->huber_delta = 0.05f;
+  o->lam_dir = 0.f;
+  o->w_alpha = o->w_beta = o->w_blr = o->w_tv = 1e-3f;
+  o->tv_eps = 1e-6f;
+  o->sigma_init = 0.05f;
+  o->lr = 1e-2f;
+  o->beta1 = 0.9f;
+  o->beta2 = 0.999f;
+  o->eps = 1e-8f;
+  o->fused = 1;
+  o->use_graph = 1;
+  o->threads_per_voxel = 0;
+  o->cta_threads = 0;
+  o->autotune = 0;
+  o->seed = 0;
+}
+
+extern "C" const char* prism_last_error(void) { return g_err.c_str(); }
+
+namespace {
+
+bool finite_nonneg(float x) { return std::isfinite(x) && x >= 0.f; }
+
+int validate_options(const prism_options& o) {
+  if (o.K < 1 || o.K > PRISM_MAX_K) return fail(PRISM_E_INVALID_ARG, "K must be in 1..5");
+  if (o.loss != PRISM_LOSS_MSE && o.loss != PRISM_LOSS_NLL) return fail(PRISM_E_INVALID_ARG, "loss must be MSE (0) or NLL (1)");
+  if (o.calibration != 0 && o.calibration != 1) return fail(PRISM_E_INVALID_ARG, "calibration must be 0 or 1");
+  if (o.patch_dim < 1 || o.patch_dim > 64) return fail(PRISM_E_INVALID_ARG, "patch_dim must be in 1..64");
+  const float nn[] = {o.lam_rep, o.lam_sparse, o.tau, o.lam_sp, o.lam_dir, o.w_alpha, o.w_beta, o.w_blr, o.w_tv};
+  for (float x : nn)
+    if (!finite_nonneg(x)) return fail(PRISM_E_INVALID_ARG, "prior weights and tau must be finite and >= 0");
+  if (!(o.huber_delta > 0.f) || !std::isfinite(o.huber_delta)) return fail(PRISM_E_INVALID_ARG, "huber_delta must be > 0");
+  if (!(o.tv_eps > 0.f)) return fail(PRISM_E_INVALID_ARG, "tv_eps must be > 0");
+  if (!(o.sigma_init > 0.f) || !std::isfinite(o.sigma_init)) return fail(PRISM_E_INVALID_ARG, "sigma_init must be > 0");
+  if (!(o.lr > 0.f) || !std::isfinite(o.lr)) return fail(PRISM_E_INVALID_ARG, "lr must be > 0");
+  if (!(o.beta1 >= 0.f && o.beta1 < 1.f) || !(o.beta2 >= 0.f && o.beta2 < 1.f))
+    return fail(PRISM_E_INVALID_ARG, "Adam betas must be in [0, 1)");
+  if (!(o.eps > 0.f)) return fail(PRISM_E_INVALID_ARG, "Adam eps must be > 0");
+  if (o.threads_per_voxel != 0 && o.threads_per_voxel != 1 && o.threads_per_voxel != 4 && o.threads_per_voxel != 16)
+    return fail(PRISM_E_INVALID_ARG, "threads_per_voxel must be 0, 1, 4 or 16");
+  if (o.cta_threads != 0 && o.cta_threads != 128 && o.cta_threads != 256)
+    return fail(PRISM_E_INVALID_ARG, "cta_threads must be 0, 128 or 256");
+  return PRISM_OK;
+}
+
+int validate_volume(const prism_volume& v, int g) {
+  const std::string w = "volume " + std::to_string(g) + ": ";
+  if (!v.mask || !v.signal || !v.bvals || !v.bvecs) return fail(PRISM_E_INVALID_ARG, w + "mask, signal, bvals and bvecs are required");
+  if (v.nx < 1 || v.ny < 1 || v.nz < 1 || v.nx > 1023 || v.ny > 1023 || v.nz > 1023)
+    return fail(PRISM_E_SHAPE, w + "grid sizes must be in 1..1023");
+  if (v.n_meas < 1 || v.n_meas > 1024) return fail(PRISM_E_SHAPE, w + "n_meas must be in 1..1024");
+  if (v.mem != PRISM_MEM_HOST && v.mem != PRISM_MEM_DEVICE) return fail(PRISM_E_INVALID_ARG, w + "mem must be HOST or DEVICE");
+  int nb0 = 0;
+  for (int n = 0; n < v.n_meas; ++n) {
+    const float b = v.bvals[n];
+    if (!std::isfinite(b) || b < 0.f) return fail(PRISM_E_INVALID_ARG, w + "b-values must be finite and >= 0");
+    const float gx = v.bvecs[3 * n], gy = v.bvecs[3 * n + 1], gz = v.bvecs[3 * n + 2];
+    if (!std::isfinite(gx) || !std::isfinite(gy) || !std::isfinite(gz)) return fail(PRISM_E_INVALID_ARG, w + "non-finite b-vector");
+    if (b <= 50.f) {
+      ++nb0;
+    } else if (std::fabs(std::sqrt(gx * gx + gy * gy + gz * gz) - 1.f) > 1e-3f) {
+      return fail(PRISM_E_INVALID_ARG, w + "b-vector " + std::to_string(n) + " of a b > 50 measurement is not unit length");
+    }
+  }
+  if (nb0 == 0) return fail(PRISM_E_SHAPE, w + "no b <= 50 measurement to normalise by");
+  return PRISM_OK;
+}
+
+void fill_args(prism_handle* h) {
+  IterArgs& a = h->ia;
+  a.Q = h->Q;
+  a.Vpad = h->Vpad;
+  a.TV = h->TV;
+  a.ntiles = h->ntiles;
+  a.Nmax = h->Nmax;
+  a.G = h->G;
+  a.tiles = h->d_tiles;
+  a.groups = h->d_groups;
+  a.y = h->d_y;
+  a.theta = h->d_theta;
+  a.m = h->d_m;
+  a.v = h->d_v;
+  a.xf = h->d_xf;
+  a.hsp = h->d_hsp;
+  a.lp = h->d_lp;
+  a.nbr = h->d_nbr;
+  a.vcoord = h->d_vcoord;
+  a.vflag = h->d_vflag;
+  a.table = h->d_table;
+  a.gparams = h->d_gparams;
+  a.gU = h->d_gU;
+  a.tile_ab = h->d_tile_ab;
+  a.tile_red = h->d_tile_red;
+  a.queue = h->d_queue;
+  a.done = h->d_done;
+  a.step = h->d_step;
+  a.adamc = h->d_adamc;
+  a.status = h->d_status;
+  const prism_options& o = h->opt;
+  a.lam_rep = o.lam_rep;
+  a.lam_sparse = o.lam_sparse;
+  a.tau = o.tau;
+  a.lam_sp = o.lam_sp;
+  a.huber_delta = o.huber_delta;
+  a.lam_dir = o.lam_dir;
+  a.w_tv = o.calibration ? o.w_tv : 0.f;
+  a.tv_eps = o.tv_eps;
+  a.lr = o.lr;
+  a.beta1 = o.beta1;
+  a.beta2 = o.beta2;
+  a.eps = o.eps;
+  a.nb_priors = h->nb ? 1 : 0;
+
+  GroupArgs& g = h->ga;
+  g.G = h->G;
+  g.max_split = h->max_split;
+  g.split_tiles = kSplitTiles;
+  g.max_e = h->max_e;
+  g.split_off = h->d_split_off;
+  g.part2 = h->d_part2;
+  g.counters = h->d_counters;
+  g.gred = h->d_gred;
+  g.gloss = h->d_gloss;
+  g.gprior = h->d_gprior;
+  g.gm = h->d_gm;
+  g.gv = h->d_gv;
+  g.gparams = h->d_gparams;
+  g.table = h->d_table;
+  g.slot_of_grid = h->d_slot_of_grid;
+  g.hist = h->d_hist;
+  g.hist_len = kHistLen;
+  g.gexport = nullptr;
+  g.loss_mode = o.loss;
+  g.w_alpha = o.w_alpha;
+  g.w_beta = o.w_beta;
+  g.w_blr = o.w_blr;
+}
+
+// Enqueues one fused iteration.
+int enqueue_fused_iter(prism_handle* h, cudaStream_t st) {
+  const IterArgs& a = h->ia;
+  if (h->opt.lam_sp > 0.f) CK(h->ks->prior_prep(a, 0, h->ntiles, st));
+  CK(h->ks->fused(a, h->opt.loss, h->cal ? 1 : 0, h->TPV, h->fused_grid, h->NT, h->fused_smem, st));
+  if (h->cal) CK(launch_bias_grad(a, h->ga, st));
+  CK(launch_group_reduce(a, h->ga, 1 | (h->cal ? 2 : 0), st));
+  CK(launch_group_adam(a, h->ga, 1 | 2, st));
+  return PRISM_OK;
+}
+
+// Enqueues one plain iteration: separate synthesis, loss, adjoint, prior and Adam launches
+// per patch, then the group update.
+int enqueue_plain_iter(prism_handle* h, cudaStream_t st) {
+  const IterArgs& a = h->ia;
+  const int cal = h->cal ? 1 : 0;
+  for (const PatchRange& pr : h->patches) {
+    PlainArgs p{h->d_yhat, h->d_r, h->d_grad, pr.tb, pr.te, 3};
+    CK(h->ks->transform(a, pr.tb, pr.te, st));
+    CK(h->ks->synth(a, p, cal, h->TPV, h->NT, st));
+    CK(launch_loss(a, p, h->opt.loss, st));
+    if (h->opt.lam_sp > 0.f) CK(h->ks->prior_prep(a, pr.tb, pr.te, st));
+    CK(h->ks->adjoint(a, p, cal, h->TPV, h->NT, h->adj_smem, st));
+    CK(h->ks->prior(a, p, st));
+    CK(launch_adam_voxel(a, p, st));
+  }
+  if (h->cal) CK(launch_bias_grad(a, h->ga, st));
+  CK(launch_group_reduce(a, h->ga, 1 | (h->cal ? 2 : 0), st));
+  CK(launch_group_adam(a, h->ga, 1 | 2, st));
+  return PRISM_OK;
+}
+
+int capture_graph(prism_handle* h, int iters, cudaGraphExec_t* out) {
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  int rc = PRISM_OK;
+  for (int i = 0; i < iters && rc == PRISM_OK; ++i) rc = enqueue_fused_iter(h, h->cap_stream);
+  cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
+  if (rc != PRISM_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  return PRISM_OK;
+}
+
+// Host-side plan of volumes -> patches -> tiles, neighbours and flags.
+struct Plan {
+  std::vector<int32_t> slot_of_vox, vox_of_slot, nbr, slot_of_grid;
+  std::vector<uint32_t> vcoord, vflag;
+  std::vector<int64_t> row_off;
+};
+
+int build_plan(prism_handle* h, const prism_volume* vols, int n_vols, Plan& pl) {
+  const int P = h->opt.patch_dim;
+  const int TV = h->TV;
+  h->G = n_vols;
+  h->groups.assign(n_vols, GroupDev{});
+  h->vox0.assign(n_vols + 1, 0);
+  h->gp_layout.assign(4 * static_cast<size_t>(n_vols) + 1, 0);
+  h->yhat_off.assign(n_vols + 1, 0);
+  // counts
+  int64_t Vtot = 0, grid_tot = 0;
+  std::vector<std::vector<int32_t>> vidx(n_vols);
+  for (int g = 0; g < n_vols; ++g) {
+    const prism_volume& v = vols[g];
+    const int64_t ng = static_cast<int64_t>(v.nx) * v.ny * v.nz;
+    vidx[g].assign(ng, -1);
+    int32_t c = 0;
+    for (int64_t i = 0; i < ng; ++i)
+      if (v.mask[i]) vidx[g][i] = c++;
+    if (c == 0) return fail(PRISM_E_SHAPE, "volume " + std::to_string(g) + ": empty mask");
+    h->vox0[g] = Vtot;
+    Vtot += c;
+    h->groups[g].grid_off = grid_tot;
+    grid_tot += ng;
+  }
+  h->vox0[n_vols] = Vtot;
+  h->V = Vtot;
+  pl.slot_of_vox.assign(Vtot, -1);
+  pl.row_off.assign(Vtot, 0);
+  pl.slot_of_grid.assign(grid_tot, -1);
+  // tiles
+  int64_t yoff = 0, aboff = 0, tab = 0, gp = 0, yh = 0;
+  int Nmax = 0;
+  for (int g = 0; g < n_vols; ++g) {
+    const prism_volume& v = vols[g];
+    GroupDev& gr = h->groups[g];
+    gr.nx = v.nx;
+    gr.ny = v.ny;
+    gr.nz = v.nz;
+    gr.N = v.n_meas;
+    gr.N4 = (v.n_meas + 3) / 4 * 4;
+    gr.n_vox = static_cast<int32_t>(h->vox0[g + 1] - h->vox0[g]);
+    gr.inv_M = 1.f / static_cast<float>(gr.n_vox);
+    gr.calib = h->cal ? 1 : 0;
+    gr.table_off = static_cast<int32_t>(tab);
+    tab += v.n_meas;
+    gr.gp_off = static_cast<int32_t>(gp);
+    h->gp_layout[4 * g + 0] = gp;
+    h->gp_layout[4 * g + 1] = gp + 4;
+    h->gp_layout[4 * g + 2] = gp + 4 + gr.N4;
+    h->gp_layout[4 * g + 3] = gp + 4 + 2 * gr.N4;
+    gp += 4 + 2 * gr.N4 + kNGrid;
+    h->yhat_off[g] = yh;
+    yh += static_cast<int64_t>(gr.n_vox) * v.n_meas;
+    Nmax = std::max(Nmax, v.n_meas);
+    gr.tile0 = static_cast<int32_t>(h->tiles.size());
+    const int px = (v.nx + P - 1) / P, py = (v.ny + P - 1) / P, pz = (v.nz + P - 1) / P;
+    std::vector<int64_t> pv;
+    for (int a = 0; a < px; ++a)
+      for (int b = 0; b < py; ++b)
+        for (int c = 0; c < pz; ++c) {
+          pv.clear();
+          for (int x = a * P; x < std::min(v.nx, (a + 1) * P); ++x)
+            for (int y = b * P; y < std::min(v.ny, (b + 1) * P); ++y)
+              for (int z = c * P; z < std::min(v.nz, (c + 1) * P); ++z) {
+                const int64_t gi = (static_cast<int64_t>(x) * v.ny + y) * v.nz + z;
+                if (vidx[g][gi] >= 0) pv.push_back(gi);
+              }
+          if (pv.empty()) continue;
+          const int pid = static_cast<int>(h->patches.size());
+          const int tb = static_cast<int>(h->tiles.size());
+          for (size_t s0 = 0; s0 < pv.size(); s0 += TV) {
+            Tile t{};
+            t.group = g;
+            t.patch = pid;
+            t.slot0 = static_cast<int32_t>(h->tiles.size()) * TV;
+            t.count = static_cast<int32_t>(std::min<size_t>(TV, pv.size() - s0));
+            t.y_off = yoff;
+            t.ab_off = static_cast<int32_t>(aboff);
+            t.n_meas = v.n_meas;
+            yoff += static_cast<int64_t>(v.n_meas) * TV;
+            aboff += 2 * v.n_meas;
+            for (int i = 0; i < t.count; ++i) {
+              const int64_t gi = pv[s0 + i];
+              const int64_t vg = h->vox0[g] + vidx[g][gi];
+              const int slot = t.slot0 + i;
+              pl.slot_of_vox[vg] = slot;
+              pl.slot_of_grid[gr.grid_off + gi] = slot;
+              pl.row_off[vg] = h->yhat_off[g] + static_cast<int64_t>(vidx[g][gi]) * v.n_meas;
+            }
+            h->tiles.push_back(t);
+          }
+          h->patches.push_back({tb, static_cast<int>(h->tiles.size())});
+        }
+    gr.ntiles = static_cast<int32_t>(h->tiles.size()) - gr.tile0;
+  }
+  h->ntiles = static_cast<int>(h->tiles.size());
+  if (static_cast<int64_t>(h->ntiles) * TV > (1LL << 31) - 1) return fail(PRISM_E_SHAPE, "too many voxels");
+  h->Vpad = h->ntiles * TV;
+  h->Nmax = Nmax;
+  h->GP = gp;
+  h->gp_layout[4 * static_cast<size_t>(n_vols)] = gp;
+  h->ypack_len = yoff;
+  h->ab_len = aboff;
+  h->tab_rows = tab;
+  h->yhat_off[n_vols] = yh;
+  h->yhat_len = yh;
+  // per-slot data
+  const int Vp = h->Vpad;
+  pl.vox_of_slot.assign(Vp, -1);
+  pl.vcoord.assign(Vp, 0);
+  pl.vflag.assign(Vp, 0);
+  pl.nbr.assign(6 * static_cast<size_t>(Vp), -1);
+  const int off[6][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
+  for (int g = 0; g < n_vols; ++g) {
+    const prism_volume& v = vols[g];
+    const GroupDev& gr = h->groups[g];
+    for (int x = 0; x < v.nx; ++x)
+      for (int y = 0; y < v.ny; ++y)
+        for (int z = 0; z < v.nz; ++z) {
+          const int64_t gi = (static_cast<int64_t>(x) * v.ny + y) * v.nz + z;
+          if (vidx[g][gi] < 0) continue;
+          const int slot = pl.slot_of_grid[gr.grid_off + gi];
+          pl.vox_of_slot[slot] = static_cast<int32_t>(h->vox0[g] + vidx[g][gi]);
+          pl.vcoord[slot] = static_cast<uint32_t>(x) | (static_cast<uint32_t>(y) << 10) | (static_cast<uint32_t>(z) << 20);
+          const int patch = h->tiles[slot / TV].patch;
+          uint32_t fl = 0;
+          int cnt = 0;
+          for (int e = 0; e < 6; ++e) {
+            const int xx = x + off[e][0], yy = y + off[e][1], zz = z + off[e][2];
+            if (xx < 0 || yy < 0 || zz < 0 || xx >= v.nx || yy >= v.ny || zz >= v.nz) continue;
+            const int64_t gj = (static_cast<int64_t>(xx) * v.ny + yy) * v.nz + zz;
+            if (vidx[g][gj] < 0) continue;
+            fl |= 1u << e;   // TV neighbour inside the mask (any patch)
+            const int sj = pl.slot_of_grid[gr.grid_off + gj];
+            if (h->tiles[sj / TV].patch == patch) {
+              pl.nbr[static_cast<size_t>(e) * Vp + slot] = sj;
+              ++cnt;
+            }
+          }
+          pl.vflag[slot] = fl | (static_cast<uint32_t>(cnt) << 8);
+        }
+  }
+  return PRISM_OK;
+}
+
+template <typename T>
+int upload(T* dst, const std::vector<T>& src, cudaStream_t st) {
+  if (src.empty()) return PRISM_OK;
+  CK(cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+  return PRISM_OK;
+}
+
+#define RC(x)                    \
+  do {                           \
+    int r_ = (x);                \
+    if (r_ != PRISM_OK) return r_; \
+  } while (0)
+
+int init_impl(prism_handle* h, const prism_volume* vols, int n_vols, cudaStream_t st) {
+  const prism_options& o = h->opt;
+  h->K = o.K;
+  h->Q = 4 * o.K + 5;
+  h->XF = 4 * o.K + 3;
+  h->cal = o.calibration != 0;
+  h->nb = (o.lam_sp > 0.f) || (o.lam_dir > 0.f);
+  h->ks = &kernels_for_k(o.K);
+  h->TV = h->NT / h->TPV;
+  Plan pl;
+  RC(build_plan(h, vols, n_vols, pl));
+  const int Vp = h->Vpad, Q = h->Q, G = h->G;
+  // group reduction geometry
+  h->max_e = 3 + (h->cal ? 2 * h->Nmax : 0);
+  std::vector<int32_t> split_off(G);
+  int tot_split = 0;
+  h->max_split = 1;
+  for (int g = 0; g < G; ++g) {
+    const int ns = (h->groups[g].ntiles + kSplitTiles - 1) / kSplitTiles;
+    split_off[g] = tot_split;
+    tot_split += ns;
+    h->max_split = std::max(h->max_split, ns);
+  }
+  const int nce = (h->max_e + 255) / 256;
+  // allocations
+  RC(h->alloc(&h->d_tiles, h->ntiles));
+  RC(h->alloc(&h->d_groups, G));
+  RC(h->alloc(&h->d_y, h->ypack_len));
+  RC(h->alloc(&h->d_theta, static_cast<size_t>(Q) * Vp));
+  RC(h->alloc(&h->d_m, static_cast<size_t>(Q) * Vp));
+  RC(h->alloc(&h->d_v, static_cast<size_t>(Q) * Vp));
+  RC(h->alloc(&h->d_xf, 2 * static_cast<size_t>(h->XF) * Vp));
+  RC(h->alloc(&h->d_hsp, static_cast<size_t>(h->K + 3) * Vp));
+  RC(h->alloc(&h->d_lp, Vp));
+  RC(h->alloc(&h->d_gU, Vp));
+  RC(h->alloc(&h->d_tile_ab, h->ab_len));
+  RC(h->alloc(&h->d_tile_red, 4 * static_cast<size_t>(h->ntiles)));
+  RC(h->alloc(&h->d_nbr, 6 * static_cast<size_t>(Vp)));
+  RC(h->alloc(&h->d_vcoord, Vp));
+  RC(h->alloc(&h->d_vflag, Vp));
+  RC(h->alloc(&h->d_table, h->tab_rows));
+  RC(h->alloc(&h->d_gparams, h->GP));
+  RC(h->alloc(&h->d_gm, h->GP));
+  RC(h->alloc(&h->d_gv, h->GP));
+  RC(h->alloc(&h->d_gred, h->GP));
+  RC(h->alloc(&h->d_gloss, G));
+  RC(h->alloc(&h->d_gprior, G));
+  RC(h->alloc(&h->d_hist, static_cast<size_t>(kHistLen) * G));
+  RC(h->alloc(&h->d_queue, 4));
+  RC(h->alloc(&h->d_done, 1));
+  RC(h->alloc(&h->d_step, 1));
+  RC(h->alloc(&h->d_status, 1));
+  RC(h->alloc(&h->d_adamc, 2));
+  RC(h->alloc(&h->d_slot_of_vox, h->V));
+  RC(h->alloc(&h->d_vox_of_slot, Vp));
+  RC(h->alloc(&h->d_slot_of_grid, pl.slot_of_grid.size()));
+  RC(h->alloc(&h->d_row_off, h->V));
+  RC(h->alloc(&h->d_split_off, G));
+  RC(h->alloc(&h->d_part2, static_cast<size_t>(tot_split) * h->max_e));
+  RC(h->alloc(&h->d_counters, static_cast<size_t>(G) * nce));
+  if (!o.fused) {
+    RC(h->alloc(&h->d_yhat, h->ypack_len));
+    RC(h->alloc(&h->d_r, h->ypack_len));
+  }
+  RC(h->alloc(&h->d_grad, static_cast<size_t>(Q) * Vp));
+  // zero state
+  CK(cudaMemsetAsync(h->d_theta, 0, sizeof(float) * Q * static_cast<size_t>(Vp), st));
+  CK(cudaMemsetAsync(h->d_m, 0, sizeof(float) * Q * static_cast<size_t>(Vp), st));
+  CK(cudaMemsetAsync(h->d_v, 0, sizeof(float) * Q * static_cast<size_t>(Vp), st));
+  CK(cudaMemsetAsync(h->d_xf, 0, sizeof(float) * 2 * h->XF * static_cast<size_t>(Vp), st));
+  CK(cudaMemsetAsync(h->d_hsp, 0, sizeof(float) * (h->K + 3) * static_cast<size_t>(Vp), st));
+  CK(cudaMemsetAsync(h->d_lp, 0, sizeof(float) * Vp, st));
+  CK(cudaMemsetAsync(h->d_gU, 0, sizeof(float) * Vp, st));
+  CK(cudaMemsetAsync(h->d_tile_ab, 0, sizeof(float) * std::max<int64_t>(h->ab_len, 1), st));
+  CK(cudaMemsetAsync(h->d_tile_red, 0, sizeof(double) * 4 * h->ntiles, st));
+  CK(cudaMemsetAsync(h->d_gparams, 0, sizeof(float) * h->GP, st));
+  CK(cudaMemsetAsync(h->d_gm, 0, sizeof(float) * h->GP, st));
+  CK(cudaMemsetAsync(h->d_gv, 0, sizeof(float) * h->GP, st));
+  CK(cudaMemsetAsync(h->d_gred, 0, sizeof(double) * h->GP, st));
+  CK(cudaMemsetAsync(h->d_gloss, 0, sizeof(double) * G, st));
+  CK(cudaMemsetAsync(h->d_gprior, 0, sizeof(double) * G, st));
+  CK(cudaMemsetAsync(h->d_hist, 0, sizeof(double) * kHistLen * G, st));
+  CK(cudaMemsetAsync(h->d_queue, 0, sizeof(int32_t) * 4, st));
+  CK(cudaMemsetAsync(h->d_done, 0, sizeof(int32_t), st));
+  CK(cudaMemsetAsync(h->d_step, 0, sizeof(int32_t), st));
+  CK(cudaMemsetAsync(h->d_status, 0, sizeof(int32_t), st));
+  CK(cudaMemsetAsync(h->d_counters, 0, sizeof(int32_t) * G * nce, st));
+  CK(cudaMemsetAsync(h->d_grad, 0, sizeof(float) * Q * static_cast<size_t>(Vp), st));
+  // metadata
+  RC(upload(h->d_tiles, h->tiles, st));
+  RC(upload(h->d_groups, h->groups, st));
+  RC(upload(h->d_nbr, pl.nbr, st));
+  RC(upload(h->d_vcoord, pl.vcoord, st));
+  RC(upload(h->d_vflag, pl.vflag, st));
+  RC(upload(h->d_slot_of_vox, pl.slot_of_vox, st));
+  RC(upload(h->d_vox_of_slot, pl.vox_of_slot, st));
+  RC(upload(h->d_slot_of_grid, pl.slot_of_grid, st));
+  RC(upload(h->d_row_off, pl.row_off, st));
+  RC(upload(h->d_split_off, split_off, st));
+  fill_args(h);
+  // per volume: b0 statistics, packing, table, sigma, parameters
+  int* d_bad = nullptr;
+  RC(h->alloc(&d_bad, 1));
+  CK(cudaMemsetAsync(d_bad, 0, sizeof(int), st));
+  for (int g = 0; g < G; ++g) {
+    const prism_volume& v = vols[g];
+    const GroupDev& gr = h->groups[g];
+    const int N = v.n_meas;
+    const int64_t Vg = gr.n_vox;
+    const float* sig = v.signal;
+    float* tmp_sig = nullptr;
+    if (v.mem == PRISM_MEM_HOST) {
+      RC(h->alloc(&tmp_sig, static_cast<size_t>(Vg) * N));
+      CK(cudaMemcpyAsync(tmp_sig, v.signal, sizeof(float) * Vg * N, cudaMemcpyHostToDevice, st));
+      sig = tmp_sig;
+    }
+    std::vector<uint8_t> isb0(N);
+    std::vector<float> bv(v.bvals, v.bvals + N), bvec(v.bvecs, v.bvecs + 3 * N);
+    int nb0 = 0;
+    for (int n = 0; n < N; ++n) {
+      isb0[n] = v.bvals[n] <= 50.f;
+      nb0 += isb0[n];
+    }
+    uint8_t* d_isb0 = nullptr;
+    float *d_bv = nullptr, *d_bvec = nullptr, *d_b0 = nullptr;
+    double* d_part = nullptr;
+    const int nbk = static_cast<int>((Vg + 255) / 256);
+    RC(h->alloc(&d_isb0, N));
+    RC(h->alloc(&d_bv, N));
+    RC(h->alloc(&d_bvec, 3 * N));
+    RC(h->alloc(&d_b0, Vg));
+    RC(h->alloc(&d_part, nbk));
+    RC(upload(d_isb0, isb0, st));
+    RC(upload(d_bv, bv, st));
+    RC(upload(d_bvec, bvec, st));
+    CK(launch_b0_stats(sig, Vg, N, d_isb0, nb0, d_b0, d_part, d_bad, st));
+    CK(launch_sigma_init(d_part, nbk, Vg, nb0, o.sigma_init, h->d_gparams + gr.gp_off, st));
+    CK(launch_pack(h->ia, sig, d_b0, h->d_vox_of_slot, h->vox0[g], gr.tile0, gr.tile0 + gr.ntiles, N, h->d_y, d_bad, st));
+    CK(launch_table(d_bv, d_bvec, N, h->d_table + gr.table_off, st));
+    if (v.init) {
+      const float* in = v.init;
+      float* tmp_in = nullptr;
+      if (v.mem == PRISM_MEM_HOST) {
+        RC(h->alloc(&tmp_in, static_cast<size_t>(Vg) * Q));
+        CK(cudaMemcpyAsync(tmp_in, v.init, sizeof(float) * Vg * Q, cudaMemcpyHostToDevice, st));
+        in = tmp_in;
+      }
+      CK(launch_scatter_params(in, h->d_slot_of_vox + h->vox0[g], Vg, Q, Vp, h->d_theta, st));
+    } else {
+      CK(launch_default_init(h->d_slot_of_vox + h->vox0[g], Vg, h->K, Vp,
+                             static_cast<uint64_t>(o.seed) * 1315423911ull + g, h->d_theta, st));
+    }
+    // free per-volume temporaries (after the work that reads them)
+    CK(cudaStreamSynchronize(st));
+    for (void* p : {static_cast<void*>(tmp_sig), static_cast<void*>(d_isb0), static_cast<void*>(d_bv),
+                    static_cast<void*>(d_bvec), static_cast<void*>(d_b0), static_cast<void*>(d_part)}) {
+      if (!p) continue;
+      auto it = std::find(h->allocs.begin(), h->allocs.end(), p);
+      if (it != h->allocs.end()) h->allocs.erase(it);
+      cudaFree(p);
+    }
+  }
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (bad > 0)
+    return fail(PRISM_E_NONFINITE, std::to_string(bad) + " voxel(s) with a non-finite signal or a non-positive b0 mean");
+  CK(h->ks->transform(h->ia, 0, h->ntiles, st));
+  CK(launch_adam_constants(h->ia, st));
+  // launch geometry of the fused kernel
+  const int NW = h->NT / 32;
+  h->fused_smem = static_cast<size_t>(h->Nmax) * sizeof(MeasRow) +
+                  (h->cal ? kNGrid * sizeof(float) + static_cast<size_t>(NW) * 2 * h->Nmax * sizeof(float) : 0);
+  h->adj_smem = h->cal ? static_cast<size_t>(NW) * 2 * h->Nmax * sizeof(float) : 0;
+  if (o.fused) {
+    int dev = 0, sms = 0, bps = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CK(h->ks->fused_occupancy(o.loss, h->cal ? 1 : 0, h->TPV, h->NT, h->fused_smem, &bps));
+    if (bps < 1) return fail(PRISM_E_CUDA, "fused kernel does not fit on an SM");
+    h->fused_grid = std::max(1, std::min(h->ntiles, sms * bps));
+  }
+  CK(cudaStreamSynchronize(st));
+  return PRISM_OK;
+}
+
+int choose_shape(const prism_options& o, int64_t V, int* tpv, int* nt) {
+  *tpv = o.threads_per_voxel ? o.threads_per_voxel : (V >= 32768 ? 1 : (V >= 4096 ? 4 : 16));
+  *nt = o.cta_threads ? o.cta_threads : 128;
+  return PRISM_OK;
+}
+
+int64_t count_voxels(const prism_volume* vols, int n) {
+  int64_t V = 0;
+  for (int g = 0; g < n; ++g) {
+    const int64_t ng = static_cast<int64_t>(vols[g].nx) * vols[g].ny * vols[g].nz;
+    for (int64_t i = 0; i < ng; ++i) V += vols[g].mask[i] != 0;
+  }
+  return V;
+}
+
+int build_graphs(prism_handle* h) {
+  CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  RC(capture_graph(h, 1, &h->g1));
+  RC(capture_graph(h, kGraphUnroll, &h->gU));
+  return PRISM_OK;
+}
+
+int create_handle(const prism_volume* vols, int n_vols, const prism_options& o, int tpv, int nt,
+                  cudaStream_t st, prism_handle** out) {
+  std::unique_ptr<prism_handle> h(new (std::nothrow) prism_handle());
+  if (!h) return fail(PRISM_E_OOM, "host allocation failed");
+  h->opt = o;
+  h->TPV = tpv;
+  h->NT = nt;
+  RC(init_impl(h.get(), vols, n_vols, st));
+  if (o.fused && o.use_graph) RC(build_graphs(h.get()));
+  *out = h.release();
+  return PRISM_OK;
+}
+
+}  // namespace
+
+extern "C" int prism_fit_init(const prism_volume* vols, int32_t n_vols, const prism_options* opt, void* stream,
+                              prism_handle** out) {
+  g_err.clear();
+  if (!out) return fail(PRISM_E_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!vols || n_vols < 1) return fail(PRISM_E_INVALID_ARG, "at least one volume is required");
+  prism_options o;
+  if (opt) o = *opt;
+  else prism_default_options(&o);
+  RC(validate_options(o));
+  for (int g = 0; g < n_vols; ++g) RC(validate_volume(vols[g], g));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t V = count_voxels(vols, n_vols);
+  int tpv = 1, nt = 128;
+  choose_shape(o, V, &tpv, &nt);
+  if (o.autotune && o.fused) {
+    // Time each candidate tile shape for a few iterations on the real data; keep the fastest.
+    const int cands[6][2] = {{1, 128}, {1, 256}, {4, 128}, {4, 256}, {16, 128}, {16, 256}};
+    float best = 1e30f;
+    prism_options oc = o;
+    oc.use_graph = 0;
+    oc.autotune = 0;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (const auto& c : cands) {
+      if (o.threads_per_voxel && c[0] != o.threads_per_voxel) continue;
+      if (o.cta_threads && c[1] != o.cta_threads) continue;
+      prism_handle* hc = nullptr;
+      if (create_handle(vols, n_vols, oc, c[0], c[1], st, &hc) != PRISM_OK) {
+        g_err.clear();
+        continue;
+      }
+      int rc = enqueue_fused_iter(hc, st);
+      cudaEventRecord(e0, st);
+      for (int i = 0; i < 3 && rc == PRISM_OK; ++i) rc = enqueue_fused_iter(hc, st);
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      delete hc;
+      if (rc == PRISM_OK && ms < best) {
+        best = ms;
+        tpv = c[0];
+        nt = c[1];
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    g_err.clear();
+  }
+  prism_handle* h = nullptr;
+  const int rc = create_handle(vols, n_vols, o, tpv, nt, st, &h);
+  if (rc != PRISM_OK) return rc;
+  *out = h;
+  return PRISM_OK;
+}
+
+extern "C" int prism_step(prism_handle* h, int32_t n_iters, void* stream) {
+  if (!h) return fail(PRISM_E_INVALID_ARG, "handle is NULL");
+  if (n_iters < 0) return fail(PRISM_E_INVALID_ARG, "n_iters must be >= 0");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  h->forward_done = false;
+  if (h->opt.fused && h->gU) {
+    int n = n_iters;
+    while (n >= kGraphUnroll) {
+      CK(cudaGraphLaunch(h->gU, st));
+      n -= kGraphUnroll;
+    }
+    for (; n > 0; --n) CK(cudaGraphLaunch(h->g1, st));
+  } else {
+    for (int i = 0; i < n_iters; ++i) RC(h->opt.fused ? enqueue_fused_iter(h, st) : enqueue_plain_iter(h, st));
+  }
+  h->iters += n_iters;
+  return PRISM_OK;
+}
+
+extern "C" int prism_sync(prism_handle* h, void* stream) {
+  if (!h) return fail(PRISM_E_INVALID_ARG, "handle is NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CK(cudaStreamSynchronize(st));
+  CK(cudaGetLastError());
+  int status = 0;
+  CK(cudaMemcpy(&status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (status & kStTimeout) return fail(PRISM_E_TIMEOUT, "a bounded device wait (table bulk copy) timed out");
+  if (status & kStNonfinite) return fail(PRISM_E_NONFINITE, "the objective became non-finite");
+  return PRISM_OK;
+}
+
+extern "C" int prism_info(const prism_handle* h, int64_t* n_vox, int32_t* n_groups, int32_t* q,
+                          int64_t* n_group_params, int64_t* iterations) {
+  if (!h) return fail(PRISM_E_INVALID_ARG, "handle is NULL");
+  if (n_vox) *n_vox = h->V;
+  if (n_groups) *n_groups = h->G;
+  if (q) *q = h->Q;
+  if (n_group_params) *n_group_params = h->GP;
+  if (iterations) *iterations = h->iters;
+  return PRISM_OK;
+}
+
+extern "C" int prism_get_params(prism_handle* h, float* out, int32_t mem, void* stream) {
+  if (!h || !out) return fail(PRISM_E_INVALID_ARG, "NULL argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t n = static_cast<size_t>(h->V) * h->Q;
+  if (mem == PRISM_MEM_DEVICE) {
+    CK(launch_gather_params(h->d_theta, h->d_slot_of_vox, h->V, h->Q, h->Vpad, out, st));
+    return PRISM_OK;
+  }
+  if (mem != PRISM_MEM_HOST) return fail(PRISM_E_INVALID_ARG, "mem must be HOST or DEVICE");
+  float* tmp = nullptr;
+  CK(cudaMalloc(&tmp, n * sizeof(float)));
+  cudaError_t e = launch_gather_params(h->d_theta, h->d_slot_of_vox, h->V, h->Q, h->Vpad, tmp, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, n * sizeof(float), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(tmp);
+  if (e != cudaSuccess) return cuda_fail(e, "prism_get_params");
+  return PRISM_OK;
+}
+
+extern "C" int prism_set_params(prism_handle* h, const float* in, int32_t mem, void* stream) {
+  if (!h || !in) return fail(PRISM_E_INVALID_ARG, "NULL argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t n = static_cast<size_t>(h->V) * h->Q;
+  const float* src = in;
+  float* tmp = nullptr;
+  if (mem == PRISM_MEM_HOST) {
+    CK(cudaMalloc(&tmp, n * sizeof(float)));
+    CK(cudaMemcpyAsync(tmp, in, n * sizeof(float), cudaMemcpyHostToDevice, st));
+    src = tmp;
+  } else if (mem != PRISM_MEM_DEVICE) {
+    return fail(PRISM_E_INVALID_ARG, "mem must be HOST or DEVICE");
+  }
+  cudaError_t e = launch_scatter_params(src, h->d_slot_of_vox, h->V, h->Q, h->Vpad, h->d_theta, st);
+  if (e == cudaSuccess) e = h->ks->transform(h->ia, 0, h->ntiles, st);
+  if (tmp) {
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(tmp);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "prism_set_params");
+  h->forward_done = false;
+  return PRISM_OK;
+}
+
+extern "C" int prism_group_layout(const prism_handle* h, int64_t* off) {
+  if (!h || !off) return fail(PRISM_E_INVALID_ARG, "NULL argument");
+  std::memcpy(off, h->gp_layout.data(), h->gp_layout.size() * sizeof(int64_t));
+  return PRISM_OK;
+}
+
+extern "C" int prism_get_groups(prism_handle* h, float* out, int32_t mem, void* stream) {
+  if (!h || !out) return fail(PRISM_E_INVALID_ARG, "NULL argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const cudaMemcpyKind k = (mem == PRISM_MEM_HOST) ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  CK(cudaMemcpyAsync(out, h->d_gparams, h->GP * sizeof(float), k, st));
+  if (mem == PRISM_MEM_HOST) CK(cudaStreamSynchronize(st));
+  return PRISM_OK;
+}
+
+extern "C" int prism_set_groups(prism_handle* h, const float* in, int32_t mem, void* stream) {
+  if (!h || !in) return fail(PRISM_E_INVALID_ARG, "NULL argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const cudaMemcpyKind k = (mem == PRISM_MEM_HOST) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  CK(cudaMemcpyAsync(h->d_gparams, in, h->GP * sizeof(float), k, st));
+  CK(launch_table_refresh(h->ga, h->ia, st));
+  if (mem == PRISM_MEM_HOST) CK(cudaStreamSynchronize(st));
+  h->forward_done = false;
+  return PRISM_OK;
+}
+
+extern "C" int prism_get_loss(prism_handle* h, double* loss, double* hist, int32_t max_iters, int32_t* n_written) {
+  if (!h) return fail(PRISM_E_INVALID_ARG, "handle is NULL");
+  RC(prism_sync(h, nullptr));
+  if (loss) CK(cudaMemcpy(loss, h->d_gloss, sizeof(double) * h->G, cudaMemcpyDeviceToHost));
+  int32_t nw = 0;
+  if (hist && max_iters > 0) {
+    int step = 0;
+    CK(cudaMemcpy(&step, h->d_step, sizeof(int), cudaMemcpyDeviceToHost));
+    const int avail = std::min<int>(step, kHistLen);
+    nw = std::min<int>(avail, max_iters);
+    std::vector<double> ring(static_cast<size_t>(kHistLen) * h->G);
+    CK(cudaMemcpy(ring.data(), h->d_hist, ring.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < nw; ++i) {
+      const int it = step - nw + i;
+      std::memcpy(hist + static_cast<size_t>(i) * h->G, ring.data() + static_cast<size_t>(it % kHistLen) * h->G,
+                  sizeof(double) * h->G);
+    }
+  }
+  if (n_written) *n_written = nw;
+  return PRISM_OK;
+}
+
+extern "C" int prism_forward(prism_handle* h, const float* theta, const float* groups, float* yhat, double* loss,
+                             void* stream) {
+  if (!h) return fail(PRISM_E_INVALID_ARG, "handle is NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!h->d_yhat) RC(h->alloc(&h->d_yhat, h->ypack_len));
+  if (!h->d_r) RC(h->alloc(&h->d_r, h->ypack_len));
+  if (theta) CK(launch_scatter_params(theta, h->d_slot_of_vox, h->V, h->Q, h->Vpad, h->d_theta, st));
+  if (groups) {
+    CK(cudaMemcpyAsync(h->d_gparams, groups, h->GP * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    CK(launch_table_refresh(h->ga, h->ia, st));
+  }
+  const IterArgs& a = h->ia;
+  PlainArgs p{h->d_yhat, h->d_r, h->d_grad, 0, h->ntiles, 1};
+  const int cal = h->cal ? 1 : 0;
+  CK(h->ks->transform(a, 0, h->ntiles, st));
+  CK(h->ks->synth(a, p, cal, h->TPV, h->NT, st));
+  CK(launch_loss(a, p, h->opt.loss, st));
+  if (h->opt.lam_sp > 0.f) CK(h->ks->prior_prep(a, 0, h->ntiles, st));
+  CK(h->ks->prior(a, p, st));
+  CK(launch_group_reduce(a, h->ga, 1, st));
+  CK(launch_group_adam(a, h->ga, 1, st));
+  if (loss) CK(cudaMemcpyAsync(loss, h->d_gloss, sizeof(double) * h->G, cudaMemcpyDeviceToDevice, st));
+  if (yhat) CK(launch_gather_yhat(h->d_yhat, a, h->d_vox_of_slot, h->d_row_off, yhat, st));
+  h->forward_done = true;
+  return PRISM_OK;
+}
+
+extern "C" int prism_backward(prism_handle* h, float* grad_theta, float* grad_groups, void* stream) {
+  if (!h) return fail(PRISM_E_INVALID_ARG, "handle is NULL");
+  if (!h->forward_done) return fail(PRISM_E_STATE, "prism_backward needs a preceding prism_forward");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const IterArgs& a = h->ia;
+  PlainArgs p{h->d_yhat, h->d_r, h->d_grad, 0, h->ntiles, 2};
+  const int cal = h->cal ? 1 : 0;
+  CK(h->ks->adjoint(a, p, cal, h->TPV, h->NT, h->adj_smem, st));
+  CK(h->ks->prior(a, p, st));
+  if (h->cal) CK(launch_bias_grad(a, h->ga, st));
+  CK(launch_group_reduce(a, h->ga, 2, st));
+  GroupArgs ga = h->ga;
+  ga.gexport = grad_groups;
+  if (grad_groups) CK(launch_group_adam(a, ga, 4, st));
+  if (grad_theta) CK(launch_gather_params(h->d_grad, h->d_slot_of_vox, h->V, h->Q, h->Vpad, grad_theta, st));
+  return PRISM_OK;
+}
+
+namespace {
+struct StateHeader {
+  uint32_t magic, version;
+  int32_t K, Q, G, step;
+  int64_t V, GP;
+};
+}  // namespace
+
+extern "C" int prism_state_size(const prism_handle* h, int64_t* bytes) {
+  if (!h || !bytes) return fail(PRISM_E_INVALID_ARG, "NULL argument");
+  *bytes = static_cast<int64_t>(sizeof(StateHeader)) + 3 * h->V * h->Q * 4 + 3 * h->GP * 4;
+  return PRISM_OK;
+}
+
+extern "C" int prism_get_state(prism_handle* h, void* host_buf, int64_t bytes, void* stream) {
+  int64_t need = 0;
+  RC(prism_state_size(h, &need));
+  if (!host_buf || bytes < need) return fail(PRISM_E_INVALID_ARG, "state buffer too small");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CK(cudaStreamSynchronize(st));
+  StateHeader hd{kStateMagic, 1, h->K, h->Q, h->G, 0, h->V, h->GP};
+  CK(cudaMemcpy(&hd.step, h->d_step, sizeof(int), cudaMemcpyDeviceToHost));
+  char* p = static_cast<char*>(host_buf);
+  std::memcpy(p, &hd, sizeof(hd));
+  p += sizeof(hd);
+  const size_t nvq = static_cast<size_t>(h->V) * h->Q;
+  float* tmp = nullptr;
+  CK(cudaMalloc(&tmp, nvq * sizeof(float)));
+  const float* srcs[3] = {h->d_theta, h->d_m, h->d_v};
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+    e = launch_gather_params(srcs[i], h->d_slot_of_vox, h->V, h->Q, h->Vpad, tmp, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p, tmp, nvq * sizeof(float), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    p += nvq * sizeof(float);
+  }
+  cudaFree(tmp);
+  if (e != cudaSuccess) return cuda_fail(e, "prism_get_state");
+  const float* gsrc[3] = {h->d_gparams, h->d_gm, h->d_gv};
+  for (int i = 0; i < 3; ++i) {
+    CK(cudaMemcpy(p, gsrc[i], h->GP * sizeof(float), cudaMemcpyDeviceToHost));
+    p += h->GP * sizeof(float);
+  }
+  return PRISM_OK;
+}
+
+extern "C" int prism_set_state(prism_handle* h, const void* host_buf, int64_t bytes, void* stream) {
+  int64_t need = 0;
+  RC(prism_state_size(h, &need));
+  if (!host_buf || bytes < need) return fail(PRISM_E_INVALID_ARG, "state buffer too small");
+  StateHeader hd;
+  const char* p = static_cast<const char*>(host_buf);
+  std::memcpy(&hd, p, sizeof(hd));
+  if (hd.magic != kStateMagic || hd.version != 1 || hd.K != h->K || hd.Q != h->Q || hd.G != h->G || hd.V != h->V ||
+      hd.GP != h->GP || hd.step < 0)
+    return fail(PRISM_E_STATE, "checkpoint does not match this problem");
+  p += sizeof(hd);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t nvq = static_cast<size_t>(h->V) * h->Q;
+  float* tmp = nullptr;
+  CK(cudaMalloc(&tmp, nvq * sizeof(float)));
+  float* dsts[3] = {h->d_theta, h->d_m, h->d_v};
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+    e = cudaMemcpyAsync(tmp, p, nvq * sizeof(float), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_scatter_params(tmp, h->d_slot_of_vox, h->V, h->Q, h->Vpad, dsts[i], st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    p += nvq * sizeof(float);
+  }
+  cudaFree(tmp);
+  if (e != cudaSuccess) return cuda_fail(e, "prism_set_state");
+  float* gdst[3] = {h->d_gparams, h->d_gm, h->d_gv};
+  for (int i = 0; i < 3; ++i) {
+    CK(cudaMemcpy(gdst[i], p, h->GP * sizeof(float), cudaMemcpyHostToDevice));
+    p += h->GP * sizeof(float);
+  }
+  CK(cudaMemcpy(h->d_step, &hd.step, sizeof(int), cudaMemcpyHostToDevice));
+  CK(launch_adam_constants(h->ia, st));
+  CK(launch_table_refresh(h->ga, h->ia, st));
+  CK(h->ks->transform(h->ia, 0, h->ntiles, st));
+  CK(cudaStreamSynchronize(st));
+  h->iters = hd.step;
+  h->forward_done = false;
+  return PRISM_OK;
+}
+
+extern "C" void prism_fit_destroy(prism_handle* h) { delete h; }
+
+extern "C" int prism_fit(const prism_volume* vols, int32_t n_vols, const prism_options* opt, int32_t n_iters,
+                         float* params_out, double* loss_out, int32_t out_mem, void* stream) {
+  if (out_mem != PRISM_MEM_HOST && out_mem != PRISM_MEM_DEVICE) return fail(PRISM_E_INVALID_ARG, "out_mem must be HOST or DEVICE");
+  prism_handle* h = nullptr;
+  RC(prism_fit_init(vols, n_vols, opt, stream, &h));
+  std::unique_ptr<prism_handle> guard(h);
+  RC(prism_step(h, n_iters, stream));
+  if (params_out) RC(prism_get_params(h, params_out, out_mem, stream));
+  RC(prism_sync(h, stream));
+  if (loss_out) {
+    if (out_mem == PRISM_MEM_HOST) {
+      RC(prism_get_loss(h, loss_out, nullptr, 0, nullptr));
+    } else {
+      CK(cudaMemcpyAsync(loss_out, h->d_gloss, sizeof(double) * h->G, cudaMemcpyDeviceToDevice,
+                         static_cast<cudaStream_t>(stream)));
+      CK(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    }
+  }
+  return PRISM_OK;
+}

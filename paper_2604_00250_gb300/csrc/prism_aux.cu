@@ -1,0 +1,469 @@
+// Non-templated PRISM kernels: preprocessing (b0 normalisation, packing, measurement
+// tables, parameter layout), the plain-path data term and Adam, and the group-level
+// reductions and updates of the calibration / noise parameters (Sec. 2.3).
+#include <math.h>
+
+#include "prism_kernels.cuh"
+#include "prism_launch.h"
+
+namespace prism {
+
+// ---------------------------------------------------------------------------
+// Preprocessing (Sec. 2.5: both y and y_hat are divided by the measured b0).
+// ---------------------------------------------------------------------------
+__global__ void k_b0_stats(const float* __restrict__ sig, int64_t V, int N, const uint8_t* __restrict__ isb0,
+                           int nb0, float* __restrict__ b0mean, double* __restrict__ part, int* bad) {
+  __shared__ double s[256];
+  const int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  double acc = 0.0;
+  if (v < V) {
+    const float* row = sig + v * N;
+    double m = 0.0;
+    bool finite = true;
+    for (int n = 0; n < N; ++n) {
+      const float x = row[n];
+      if (!isfinite(x)) finite = false;
+      if (isb0[n]) m += x;
+    }
+    m /= nb0;
+    if (!finite || !(m > 0.0)) {
+      atomicAdd(bad, 1);
+      m = 1.0;
+    }
+    b0mean[v] = static_cast<float>(m);
+    for (int n = 0; n < N; ++n)
+      if (isb0[n]) {
+        const double d = row[n] / m - 1.0;
+        acc += d * d;
+      }
+  }
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+}
+
+// sigma init (reading R18): pooled std of the normalised b0 repeats, clamped >= 1e-3.
+__global__ void k_sigma_init(const double* part, int nblocks, int64_t V, int nb0, float fallback,
+                             float* sigma_log) {
+  if (threadIdx.x != 0) return;
+  double s = 0.0;
+  for (int b = 0; b < nblocks; ++b) s += part[b];
+  double sg = fallback;
+  if (nb0 >= 2) sg = fmax(sqrt(s / (static_cast<double>(V) * (nb0 - 1))), 1e-3);
+  *sigma_log = static_cast<float>(log(sg));
+}
+
+__global__ void k_pack(const IterArgs a, const float* __restrict__ sig, const float* __restrict__ b0mean,
+                       const int32_t* __restrict__ vox_of_slot, int64_t vox0, int tile_begin, int N,
+                       float* __restrict__ ypack) {
+  const int t = tile_begin + blockIdx.x;
+  const Tile tl = a.tiles[t];
+  for (int e = threadIdx.x; e < N * a.TV; e += blockDim.x) {
+    const int n = e / a.TV, vl = e - n * a.TV;
+    float val = 0.f;
+    if (vl < tl.count) {
+      const int64_t v = vox_of_slot[tl.slot0 + vl] - vox0;
+      val = sig[v * N + n] / b0mean[v];
+    }
+    ypack[tl.y_off + e] = val;
+  }
+}
+
+// Static part of the per-measurement table; exp(alpha) = 1, beta = 0 (identity, Sec. 2.3).
+__global__ void k_table(const float* bvals, const float* bvecs, int N, MeasRow* rows) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const double b = bvals[n];
+  const double L2E = 1.4426950408889634;
+  MeasRow r;
+  r.gx = bvecs[3 * n];
+  r.gy = bvecs[3 * n + 1];
+  r.gz = bvecs[3 * n + 2];
+  r.kpar = static_cast<float>(b * 1.7e-3 * L2E);    // D_par = 1.7e-3 mm^2/s (Eq. 4)
+  r.kperp = static_cast<float>(b * 0.4e-3 * L2E);   // D_perp = 0.4e-3
+  r.ecsf = static_cast<float>(exp(-b * 3.0e-3));    // Eq. 3
+  r.egm = static_cast<float>(exp(-b * 0.9e-3));
+  r.eres = static_cast<float>(exp(-b * 0.2e-3));
+  r.A = 1.f;
+  r.beta = 0.f;
+  r.dpar2 = static_cast<float>(2.0 * b * 1.7e-3);
+  r.dperp2 = static_cast<float>(2.0 * b * 0.4e-3);
+  rows[n] = r;
+}
+
+__global__ void k_scatter_params(const float* __restrict__ in, const int32_t* __restrict__ slot_of_vox,
+                                 int64_t V, int Q, int Vpad, float* __restrict__ theta) {
+  const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= V * Q) return;
+  const int64_t v = e / Q;
+  const int q = static_cast<int>(e - v * Q);
+  theta[static_cast<size_t>(q) * Vpad + slot_of_vox[v]] = in[e];
+}
+
+__global__ void k_gather_params(const float* __restrict__ theta, const int32_t* __restrict__ slot_of_vox,
+                                int64_t V, int Q, int Vpad, float* __restrict__ out) {
+  const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= V * Q) return;
+  const int64_t v = e / Q;
+  const int q = static_cast<int>(e - v * Q);
+  out[e] = theta[static_cast<size_t>(q) * Vpad + slot_of_vox[v]];
+}
+
+// Counter-based generator: splitmix64 (Steele, Lea, Flood 2014) of (seed, voxel, draw).
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+__device__ __forceinline__ double u01(uint64_t h) { return ((h >> 11) + 0.5) * (1.0 / 9007199254740992.0); }
+
+// Default start: S0 = 1, equal fractions, f_intra = 0.5, directions uniform on the sphere.
+__global__ void k_default_init(const int32_t* __restrict__ slot_of_vox, int64_t V, int K, int Vpad,
+                               uint64_t seed, float* __restrict__ theta) {
+  const int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  const int slot = slot_of_vox[v];
+  theta[slot] = static_cast<float>(log(exp(1.0) - 1.0));
+  for (int i = 0; i < K + 3; ++i) theta[static_cast<size_t>(1 + i) * Vpad + slot] = 0.f;
+  for (int k = 0; k < K; ++k) {
+    double g[3];
+    for (int c = 0; c < 3; c += 2) {
+      const uint64_t base = seed * 0x100000001B3ull ^ (static_cast<uint64_t>(v) << 8) ^ (k * 4 + c);
+      const double u1 = u01(splitmix64(base)), u2 = u01(splitmix64(base ^ 0xABCDEF12345ull));
+      const double rad = sqrt(-2.0 * log(u1));
+      g[c] = rad * cos(6.283185307179586 * u2);
+      if (c + 1 < 3) g[c + 1] = rad * sin(6.283185307179586 * u2);
+    }
+    const double nr = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]) + 1e-300;
+    for (int c = 0; c < 3; ++c) theta[static_cast<size_t>(K + 4 + 3 * k + c) * Vpad + slot] = static_cast<float>(g[c] / nr);
+  }
+  theta[static_cast<size_t>(4 * K + 4) * Vpad + slot] = 0.f;
+}
+
+__global__ void k_gather_yhat(const float* __restrict__ ypack, const IterArgs a,
+                              const int32_t* __restrict__ vox_of_slot, const int64_t* __restrict__ row_off,
+                              float* __restrict__ out) {
+  const Tile tl = a.tiles[blockIdx.x];
+  for (int e = threadIdx.x; e < tl.n_meas * a.TV; e += blockDim.x) {
+    const int n = e / a.TV, vl = e - n * a.TV;
+    if (vl >= tl.count) continue;
+    const int64_t v = vox_of_slot[tl.slot0 + vl];
+    out[row_off[v] + n] = ypack[tl.y_off + e];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Plain-path data term and voxel Adam.
+// ---------------------------------------------------------------------------
+__global__ void k_adam_voxel(const IterArgs a, const PlainArgs pa) {
+  const int slot = pa.tile_begin * a.TV + blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= pa.tile_end * a.TV) return;
+  const Tile tl = a.tiles[slot / a.TV];
+  if (slot - tl.slot0 >= tl.count) return;
+  const float stepsz = a.adamc[0], isbc2 = a.adamc[1];
+  for (int q = 0; q < a.Q; ++q) {
+    const size_t ix = static_cast<size_t>(q) * a.Vpad + slot;
+    const float g = pa.grad[ix];
+    const float mq = fmaf(a.beta1, a.m[ix], (1.f - a.beta1) * g);
+    const float vq = fmaf(a.beta2, a.v[ix], (1.f - a.beta2) * g * g);
+    a.m[ix] = mq;
+    a.v[ix] = vq;
+    a.theta[ix] -= stepsz * mq / fmaf(sqrtf(vq), isbc2, a.eps);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Group reductions: per-tile partials -> per-group sums, fixed order (two levels:
+// splits of `split_tiles` tiles, then the last-arriving block sums the splits).
+// Entries: 0 data loss, 1 dJ/dsigma_log, 2 prior loss, 3.. 3+2N alpha / beta.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_group_reduce(const IterArgs a, const GroupArgs g, int what) {
+  __shared__ int s_last;
+  const int gi = blockIdx.z, s = blockIdx.y, ce = blockIdx.x;
+  const GroupDev gr = a.groups[gi];
+  const int nsplit = (gr.ntiles + g.split_tiles - 1) / g.split_tiles;
+  if (s >= nsplit) return;
+  const int E = 3 + ((gr.calib && (what & 2)) ? 2 * gr.N : 0);
+  if (ce * 256 >= E) return;
+  const int e = ce * 256 + threadIdx.x;
+  const int t0 = gr.tile0 + s * g.split_tiles;
+  const int t1 = min(gr.tile0 + gr.ntiles, t0 + g.split_tiles);
+  double acc = 0.0;
+  if (e < E) {
+    if (e < 3) {
+      for (int t = t0; t < t1; ++t) acc += a.tile_red[4 * static_cast<size_t>(t) + e];
+    } else {
+      for (int t = t0; t < t1; ++t) acc += a.tile_ab[a.tiles[t].ab_off + (e - 3)];
+    }
+    g.part2[static_cast<size_t>(g.split_off[gi] + s) * g.max_e + e] = acc;
+  }
+  __threadfence();
+  __syncthreads();
+  const int nce = (g.max_e + 255) / 256;
+  if (threadIdx.x == 0) {
+    const int prev = atomicAdd(&g.counters[gi * nce + ce], 1);
+    s_last = (prev == nsplit - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (e < E) {
+    double tot = 0.0;
+    for (int k = 0; k < nsplit; ++k)
+      tot += __ldcg(&g.part2[static_cast<size_t>(g.split_off[gi] + k) * g.max_e + e]);
+    if (e == 0) {
+      if (what & 1) g.gloss[gi] = tot;
+    } else if (e == 1) {
+      g.gred[gr.gp_off] = tot;
+    } else if (e == 2) {
+      if (what & 1) g.gprior[gi] = tot;
+    }
+    else if (e < 3 + gr.N) g.gred[gr.gp_off + 4 + (e - 3)] = tot;
+    else g.gred[gr.gp_off + 4 + gr.N4 + (e - 3 - gr.N)] = tot;
+  }
+  if (threadIdx.x == 0) g.counters[gi * nce + ce] = 0;
+}
+
+// dJ/db_lr[c] = sum_x w_c(x) dJ/dU(x) over the voxels whose trilinear stencil holds corner c.
+__global__ void __launch_bounds__(256) k_bias_grad(const IterArgs a, const GroupArgs g) {
+  __shared__ double s[256];
+  const int gi = blockIdx.y, c = blockIdx.x;
+  const GroupDev gr = a.groups[gi];
+  if (!gr.calib) return;
+  const int cc[3] = {c / 64, (c / 8) % 8, c % 8};
+  const int n[3] = {gr.nx, gr.ny, gr.nz};
+  int lo[3], hi[3];
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    const float sc = n[ax] / 8.f;
+    lo[ax] = (cc[ax] == 0) ? 0 : max(0, static_cast<int>(floorf((cc[ax] - 0.5f) * sc - 0.5f)) - 1);
+    hi[ax] = (cc[ax] == 7) ? n[ax] - 1 : min(n[ax] - 1, static_cast<int>(ceilf((cc[ax] + 1.5f) * sc - 0.5f)) + 1);
+  }
+  const int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1, ez = hi[2] - lo[2] + 1;
+  const int tot = ex * ey * ez;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+    const int x = lo[0] + i / (ey * ez);
+    const int y = lo[1] + (i / ez) % ey;
+    const int z = lo[2] + i % ez;
+    const int slot = g.slot_of_grid[gr.grid_off + (static_cast<int64_t>(x) * gr.ny + y) * gr.nz + z];
+    if (slot < 0) continue;
+    const TriW tw = tri_weights(x, y, z, gr.nx, gr.ny, gr.nz);
+    const int b[3] = {tw.base / 64, (tw.base / 8) % 8, tw.base % 8};
+    float w = 1.f;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+      const int d = cc[ax] - b[ax];
+      w *= (d == 0) ? 1.f - tw.w[ax] : ((d == 1) ? tw.w[ax] : 0.f);
+    }
+    if (w != 0.f) acc += static_cast<double>(w) * a.gU[slot];
+  }
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) g.gred[gr.gp_off + 4 + 2 * gr.N4 + c] = s[0];
+}
+
+// Group finalisation (one block): objective with calibration regularisers (reading R11),
+// loss history, Adam on sigma_log / alpha / beta / b_lr, table refresh, step counter.
+// mode bit 0: loss; bit 1: Adam + step; bit 2: export gradients.
+__global__ void __launch_bounds__(256) k_group_adam(const IterArgs a, const GroupArgs g, int mode) {
+  __shared__ double s[256];
+  __shared__ int s_bad;
+  const int tid = threadIdx.x;
+  if (tid == 0) s_bad = 0;
+  const int step = *a.step;
+  const float stepsz = a.adamc[0], isbc2 = a.adamc[1];
+  for (int gi = 0; gi < g.G; ++gi) {
+    const GroupDev gr = a.groups[gi];
+    const int base = gr.gp_off;
+    const int N = gr.N, N4 = gr.N4;
+    // regulariser values
+    double reg = 0.0;
+    if (gr.calib) {
+      for (int i = tid; i < 2 * N + kNGrid; i += blockDim.x) {
+        float x;
+        double w;
+        if (i < N) { x = g.gparams[base + 4 + i]; w = g.w_alpha / N; }
+        else if (i < 2 * N) { x = g.gparams[base + 4 + N4 + (i - N)]; w = g.w_beta / N; }
+        else { x = g.gparams[base + 4 + 2 * N4 + (i - 2 * N)]; w = g.w_blr / kNGrid; }
+        reg += w * static_cast<double>(x) * x;
+      }
+    }
+    s[tid] = reg;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+      if (tid < o) s[tid] += s[tid + o];
+      __syncthreads();
+    }
+    if ((mode & 1) && tid == 0) {
+      const double J = g.gloss[gi] + g.gprior[gi] + s[0];
+      g.gloss[gi] = J;
+      if (!isfinite(J)) s_bad = 1;
+      if (mode & 2) g.hist[static_cast<size_t>(step % g.hist_len) * g.G + gi] = J;
+    }
+    __syncthreads();
+    // gradients and Adam over the group's packed parameters
+    const int total = 4 + 2 * N4 + kNGrid;
+    for (int i = tid; i < total; i += blockDim.x) {
+      float grad;
+      bool train;
+      const float x = g.gparams[base + i];
+      if (i == 0) {
+        train = (g.loss_mode == kLossNLL);
+        grad = train ? static_cast<float>(g.gred[base]) : 0.f;
+      } else if (i < 4) {
+        train = false;
+        grad = 0.f;
+      } else if (i < 4 + N4) {
+        train = gr.calib && (i - 4 < N);
+        grad = train ? static_cast<float>(g.gred[base + i] + 2.0 * g.w_alpha / N * x) : 0.f;
+      } else if (i < 4 + 2 * N4) {
+        train = gr.calib && (i - 4 - N4 < N);
+        grad = train ? static_cast<float>(g.gred[base + i] + 2.0 * g.w_beta / N * x) : 0.f;
+      } else {
+        train = gr.calib;
+        grad = train ? static_cast<float>(g.gred[base + i] + 2.0 * g.w_blr / kNGrid * x) : 0.f;
+      }
+      if (g.gexport && (mode & 4)) g.gexport[base + i] = grad;
+      if ((mode & 2) && train) {
+        const float mq = fmaf(a.beta1, g.gm[base + i], (1.f - a.beta1) * grad);
+        const float vq = fmaf(a.beta2, g.gv[base + i], (1.f - a.beta2) * grad * grad);
+        g.gm[base + i] = mq;
+        g.gv[base + i] = vq;
+        const float xn = x - stepsz * mq / fmaf(sqrtf(vq), isbc2, a.eps);
+        g.gparams[base + i] = xn;
+        if (i >= 4 && i < 4 + 2 * N4) {
+          const int n = (i < 4 + N4) ? i - 4 : i - 4 - N4;
+          MeasRow* row = g.table + gr.table_off + n;
+          if (i < 4 + N4) row->A = expf(xn);
+          else row->beta = xn;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if ((mode & 2) && tid == 0) {
+    if (s_bad) atomicOr(a.status, kStNonfinite);
+    *const_cast<int32_t*>(a.step) = step + 1;
+    // constants of the next iteration, t = step + 2 (bias corrections in double)
+    const double t2 = static_cast<double>(step) + 2.0;
+    float* ac = const_cast<float*>(a.adamc);
+    ac[0] = static_cast<float>(a.lr / (1.0 - pow(static_cast<double>(a.beta1), t2)));
+    ac[1] = static_cast<float>(1.0 / sqrt(1.0 - pow(static_cast<double>(a.beta2), t2)));
+  }
+}
+
+// Adam constants for the coming iteration t = step + 1 (after init or a checkpoint load).
+__global__ void k_adam_constants(const IterArgs a) {
+  if (threadIdx.x != 0) return;
+  const double t1 = static_cast<double>(*a.step) + 1.0;
+  float* ac = const_cast<float*>(a.adamc);
+  ac[0] = static_cast<float>(a.lr / (1.0 - pow(static_cast<double>(a.beta1), t1)));
+  ac[1] = static_cast<float>(1.0 / sqrt(1.0 - pow(static_cast<double>(a.beta2), t1)));
+}
+
+// Table refresh after the caller sets group parameters (exp(alpha), beta).
+__global__ void k_table_refresh(const GroupArgs g, const IterArgs a) {
+  const GroupDev gr = a.groups[blockIdx.x];
+  for (int n = threadIdx.x; n < gr.N; n += blockDim.x) {
+    MeasRow* row = g.table + gr.table_off + n;
+    row->A = gr.calib ? expf(g.gparams[gr.gp_off + 4 + n]) : 1.f;
+    row->beta = gr.calib ? g.gparams[gr.gp_off + 4 + gr.N4 + n] : 0.f;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers.
+// ---------------------------------------------------------------------------
+static inline int nblk(int64_t n, int b) { return static_cast<int>((n + b - 1) / b); }
+
+cudaError_t launch_group_reduce(const IterArgs& a, const GroupArgs& g, int what, cudaStream_t st) {
+  dim3 grid((g.max_e + 255) / 256, g.max_split, g.G);
+  k_group_reduce<<<grid, 256, 0, st>>>(a, g, what);
+  return cudaGetLastError();
+}
+cudaError_t launch_bias_grad(const IterArgs& a, const GroupArgs& g, cudaStream_t st) {
+  k_bias_grad<<<dim3(kNGrid, g.G), 256, 0, st>>>(a, g);
+  return cudaGetLastError();
+}
+cudaError_t launch_group_adam(const IterArgs& a, const GroupArgs& g, int mode, cudaStream_t st) {
+  k_group_adam<<<1, 256, 0, st>>>(a, g, mode);
+  return cudaGetLastError();
+}
+cudaError_t launch_loss(const IterArgs& a, const PlainArgs& p, int loss, cudaStream_t st) {
+  const int nt = p.tile_end - p.tile_begin;
+  if (nt <= 0) return cudaSuccess;
+  if (loss == kLossMSE) k_loss<kLossMSE><<<nt, 256, 0, st>>>(a, p);
+  else k_loss<kLossNLL><<<nt, 256, 0, st>>>(a, p);
+  return cudaGetLastError();
+}
+cudaError_t launch_adam_voxel(const IterArgs& a, const PlainArgs& p, cudaStream_t st) {
+  const int64_t n = static_cast<int64_t>(p.tile_end - p.tile_begin) * a.TV;
+  if (n <= 0) return cudaSuccess;
+  k_adam_voxel<<<nblk(n, 256), 256, 0, st>>>(a, p);
+  return cudaGetLastError();
+}
+cudaError_t launch_b0_stats(const float* sig, int64_t V, int N, const uint8_t* isb0, int nb0, float* b0mean,
+                            double* part, int* bad, cudaStream_t st) {
+  k_b0_stats<<<nblk(V, 256), 256, 0, st>>>(sig, V, N, isb0, nb0, b0mean, part, bad);
+  return cudaGetLastError();
+}
+cudaError_t launch_sigma_init(const double* part, int nblocks, int64_t V, int nb0, float fb, float* out,
+                              cudaStream_t st) {
+  k_sigma_init<<<1, 32, 0, st>>>(part, nblocks, V, nb0, fb, out);
+  return cudaGetLastError();
+}
+cudaError_t launch_pack(const IterArgs& a, const float* sig, const float* b0mean, const int32_t* vox_of_slot,
+                        int64_t vox0, int tile_begin, int tile_end, int N, float* ypack, int* bad,
+                        cudaStream_t st) {
+  (void)bad;
+  if (tile_end <= tile_begin) return cudaSuccess;
+  k_pack<<<tile_end - tile_begin, 256, 0, st>>>(a, sig, b0mean, vox_of_slot, vox0, tile_begin, N, ypack);
+  return cudaGetLastError();
+}
+cudaError_t launch_table(const float* bvals, const float* bvecs, int N, MeasRow* rows, cudaStream_t st) {
+  k_table<<<nblk(N, 128), 128, 0, st>>>(bvals, bvecs, N, rows);
+  return cudaGetLastError();
+}
+cudaError_t launch_scatter_params(const float* in, const int32_t* sov, int64_t V, int Q, int Vpad, float* th,
+                                  cudaStream_t st) {
+  if (V == 0) return cudaSuccess;
+  k_scatter_params<<<nblk(V * Q, 256), 256, 0, st>>>(in, sov, V, Q, Vpad, th);
+  return cudaGetLastError();
+}
+cudaError_t launch_gather_params(const float* th, const int32_t* sov, int64_t V, int Q, int Vpad, float* out,
+                                 cudaStream_t st) {
+  if (V == 0) return cudaSuccess;
+  k_gather_params<<<nblk(V * Q, 256), 256, 0, st>>>(th, sov, V, Q, Vpad, out);
+  return cudaGetLastError();
+}
+cudaError_t launch_default_init(const int32_t* sov, int64_t V, int K, int Vpad, uint64_t seed, float* th,
+                                cudaStream_t st) {
+  if (V == 0) return cudaSuccess;
+  k_default_init<<<nblk(V, 128), 128, 0, st>>>(sov, V, K, Vpad, seed, th);
+  return cudaGetLastError();
+}
+cudaError_t launch_gather_yhat(const float* ypack, const IterArgs& a, const int32_t* vos, const int64_t* roff,
+                               float* out, cudaStream_t st) {
+  k_gather_yhat<<<a.ntiles, 256, 0, st>>>(ypack, a, vos, roff, out);
+  return cudaGetLastError();
+}
+cudaError_t launch_adam_constants(const IterArgs& a, cudaStream_t st) {
+  k_adam_constants<<<1, 32, 0, st>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t launch_table_refresh(const GroupArgs& g, const IterArgs& a, cudaStream_t st) {
+  k_table_refresh<<<g.G, 128, 0, st>>>(g, a);
+  return cudaGetLastError();
+}
+
+}  // namespace prism

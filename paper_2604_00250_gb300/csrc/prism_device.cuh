@@ -1,0 +1,256 @@
+// Device-side data structures and helpers of the PRISM fitting kernels (sm_103a).
+//
+// Notation follows the paper: S0, fractions f (softmax over [csf, gm, wm_1..wm_K,
+// res]), fiber directions d_k, intra-axonal fraction f_in (Sec. 2.2), bias field
+// B = exp(U), U = trilinear(b_lr) (Sec. 2.3), per-measurement exp(alpha_n), beta_n,
+// noise sigma = exp(sigma_log).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "bessel_fit.h"
+
+namespace prism {
+
+constexpr int kGrid = 8;          // bias control grid edge (Sec. 2.3 item 1)
+constexpr int kNGrid = 512;
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+constexpr float kHalfLog2Pi = 0.9189385332046727f;   // log(2 pi) / 2
+constexpr float kNormEps2 = 1e-24f;                  // |v| clamp 1e-12, squared
+
+// Device status word bits (read by prism_sync).
+enum : int { kStTimeout = 1, kStNonfinite = 2 };
+
+// One row of the per-measurement table (48 bytes, 16-byte aligned for the bulk copy).
+struct __align__(16) MeasRow {
+  float gx, gy, gz, kpar;     // g_n; b_n D_par log2(e)
+  float kperp, ecsf, egm, eres;  // b_n D_perp log2(e); E_csf, E_gm, E_res at b_n (Eq. 3)
+  float A, beta, dpar2, dperp2;  // exp(alpha_n), beta_n (Eq. 5); 2 b_n D_par, 2 b_n D_perp
+};
+
+// A tile: up to TV voxels of one patch, processed by one CTA.
+struct Tile {
+  int32_t group, patch, slot0, count;
+  int64_t y_off;     // float offset of the packed [N][TV] signal block
+  int32_t ab_off;    // float offset of the tile's [2][N] alpha/beta gradient partials
+  int32_t n_meas;
+};
+
+struct GroupDev {
+  int32_t nx, ny, nz, N;
+  int32_t tile0, ntiles;
+  int32_t table_off;   // first MeasRow of the group
+  int32_t gp_off;      // packed group params: sigma_log at gp_off, alpha at +4, beta at +4+N4, b_lr at +4+2 N4
+  int32_t N4;          // N rounded up to a multiple of 4
+  int32_t n_vox;
+  float inv_M;         // 1 / |M_g|
+  int32_t calib;       // calibration learned for this group
+  int64_t grid_off;    // offset of the group's [nx][ny][nz] slot map
+  int32_t pad[2];
+};
+
+// Kernel arguments shared by the iteration kernels (passed by value).
+struct IterArgs {
+  int32_t Q, Vpad, TV, ntiles, Nmax, G;
+  const Tile* tiles;
+  const GroupDev* groups;
+  const float* y;          // packed b0-normalised signal
+  float* theta;            // [Q][Vpad]
+  float* m;                // Adam first moments [Q][Vpad]
+  float* v;                // Adam second moments [Q][Vpad]
+  float* xf;               // [2][4K+3][Vpad] fractions and unit directions (ping-pong by step parity)
+  float* hsp;              // [K+3][Vpad] rho'(u) / |N| of the Huber-Laplacian prior
+  float* lp;               // [Vpad] Huber-Laplacian prior value per voxel
+  const int32_t* nbr;      // [6][Vpad] same-patch masked neighbour slots or -1
+  const uint32_t* vcoord;  // [Vpad] x | y << 10 | z << 20
+  const uint32_t* vflag;   // [Vpad] bits 0-5 TV neighbours (+x,-x,+y,-y,+z,-z) masked; bits 8-11 |N(x)|
+  const MeasRow* table;    // per-group measurement tables
+  const float* gparams;    // packed group parameters
+  float* gU;               // [Vpad] dJ/dU(x)
+  float* tile_ab;          // per-tile [2][N] alpha / beta gradient partials
+  double* tile_red;        // per-tile [4]: data loss, dJ/dsigma_log, prior loss, spare
+  int32_t* queue;          // persistent work-queue counter
+  int32_t* done;           // CTAs finished (last one resets the queue)
+  const int32_t* step;     // iterations completed
+  const float* adamc;      // Adam step constants of the coming iteration t: lr / (1 - b1^t), 1 / sqrt(1 - b2^t)
+  int32_t* status;         // device status word
+  float lam_rep, lam_sparse, tau, lam_sp, huber_delta, lam_dir, w_tv, tv_eps;
+  float lr, beta1, beta2, eps;
+  int32_t nb_priors;       // spatial or directional prior active
+};
+
+// Auxiliary arguments of the unfused (plain) kernels.
+struct PlainArgs {
+  float* yhat;             // packed like y
+  float* r;                // packed like y: dL/dy_hat
+  float* grad;             // [Q][Vpad] raw-parameter gradient
+  int32_t tile_begin, tile_end;
+  int32_t mode;            // k_prior: bit 0 loss, bit 1 gradient
+};
+
+// ---------------------------------------------------------------------------
+// PTX helpers.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float ex2f_(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2f_(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcpf_(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// Bulk (non-tensor) TMA copy global -> shared, completing on `bar`. Both addresses
+// 16-byte aligned and `bytes` a multiple of 16 (the caller guarantees it).
+__device__ __forceinline__ void tma_bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// Bounded wait on phase `parity`; false if it did not complete within the limit.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t addr = smem_u32(bar);
+  for (int it = 0; it < (1 << 22); ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// ---------------------------------------------------------------------------
+// Scalar helpers.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float softplusf_(float s) {   // log(1 + e^s), stable
+  return fmaxf(s, 0.f) + log1pf(expf(-fabsf(s)));
+}
+__device__ __forceinline__ float sigmoidf_(float s) { return 1.f / (1.f + expf(-s)); }
+
+// Huber rho and its derivative (transition delta).
+__device__ __forceinline__ float huber_rho(float r, float dl) {
+  const float a = fabsf(r);
+  return a <= dl ? 0.5f * r * r : dl * (a - 0.5f * dl);
+}
+__device__ __forceinline__ float huber_drho(float r, float dl) {
+  return fabsf(r) <= dl ? r : copysignf(dl, r);
+}
+
+// Q(z) = 1 - I1(z)/I0(z) and L(z) = log(exp(-z) I0(z)) for z >= 0, float32.
+// Power series below PRISM_BESSEL_ZS, fitted smooth functions of ZS/z above.
+template <bool WANT_L>
+__device__ __forceinline__ void bessel_QL(float z, float& Q, float& L) {
+  if (z < PRISM_BESSEL_ZS) {
+    const float t = 0.25f * z * z;
+    float i0 = k_bessel_s0[PRISM_BESSEL_NSER - 1];
+    float i1 = k_bessel_s1[PRISM_BESSEL_NSER - 1];
+#pragma unroll
+    for (int k = PRISM_BESSEL_NSER - 2; k >= 0; --k) {
+      i0 = fmaf(i0, t, k_bessel_s0[k]);
+      i1 = fmaf(i1, t, k_bessel_s1[k]);
+    }
+    Q = 1.f - 0.5f * z * i1 / i0;
+    if (WANT_L) L = lg2f_(i0) * kLn2 - z;
+  } else {
+    const float x = PRISM_BESSEL_ZS * rcpf_(z);
+    float pb = k_bessel_pb[PRISM_BESSEL_DEG];
+#pragma unroll
+    for (int k = PRISM_BESSEL_DEG - 1; k >= 0; --k) pb = fmaf(pb, x, k_bessel_pb[k]);
+    Q = pb * x * (1.f / PRISM_BESSEL_ZS);
+    if (WANT_L) {
+      float pa = k_bessel_pa[PRISM_BESSEL_DEG];
+#pragma unroll
+      for (int k = PRISM_BESSEL_DEG - 1; k >= 0; --k) pa = fmaf(pa, x, k_bessel_pa[k]);
+      L = (lg2f_(pa) - 0.5f * lg2f_(z)) * kLn2 - kHalfLog2Pi;
+    }
+  }
+}
+
+// U(x) = trilinear upsampling of the 8^3 grid at voxel (i, j, k) of an n-grid,
+// align_corners = False: u = clamp((i + .5) 8 / n - .5, 0, 7).
+struct TriW {
+  int base;       // flat index of corner (i0, j0, k0)
+  float w[3];     // fractional parts per axis
+};
+__device__ __forceinline__ TriW tri_weights(int i, int j, int k, int nx, int ny, int nz) {
+  TriW t;
+  int idx[3];
+  const int c[3] = {i, j, k};
+  const int n[3] = {nx, ny, nz};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float u = (c[a] + 0.5f) * (8.f / n[a]) - 0.5f;
+    u = fminf(fmaxf(u, 0.f), 7.f);
+    int i0 = min(static_cast<int>(floorf(u)), 6);
+    idx[a] = i0;
+    t.w[a] = u - i0;
+  }
+  t.base = (idx[0] * kGrid + idx[1]) * kGrid + idx[2];
+  return t;
+}
+__device__ __forceinline__ float tri_eval(const float* blr, const TriW& t) {
+  float s = 0.f;
+#pragma unroll
+  for (int cx = 0; cx < 2; ++cx)
+#pragma unroll
+    for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+      for (int cz = 0; cz < 2; ++cz) {
+        const float w = (cx ? t.w[0] : 1.f - t.w[0]) * (cy ? t.w[1] : 1.f - t.w[1]) *
+                        (cz ? t.w[2] : 1.f - t.w[2]);
+        s = fmaf(w, blr[t.base + (cx * kGrid + cy) * kGrid + cz], s);
+      }
+  return s;
+}
+
+__device__ __forceinline__ void unpack_coord(uint32_t c, int& x, int& y, int& z) {
+  x = c & 1023;
+  y = (c >> 10) & 1023;
+  z = (c >> 20) & 1023;
+}
+
+// Warp reductions (xor butterfly; every lane ends with the sum).
+template <int FIRST, int LAST>
+__device__ __forceinline__ float warp_sum_range(float x) {
+#pragma unroll
+  for (int o = FIRST; o <= LAST; o <<= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+__device__ __forceinline__ double warp_sum_d(double x) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+}  // namespace prism

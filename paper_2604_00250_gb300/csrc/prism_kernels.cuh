@@ -1,0 +1,788 @@
+// Templated PRISM iteration kernels (K fibers, TPV threads per voxel, loss mode,
+// calibration on/off). Included by one translation unit per K.
+//
+// The forward model, data terms and priors follow the paper (Sec. 2.2 Eqs. 2-4,
+// Sec. 2.3 Eq. 5, Sec. 2.4, Sec. 2.5 Eqs. 7-8); the gradient is the hand-written
+// adjoint of those equations; the update is Adam (the paper's Table 2 comparator).
+#pragma once
+
+#include "prism_device.cuh"
+
+namespace prism {
+
+enum : int { kLossMSE = 0, kLossNLL = 1 };
+
+// Per-voxel transformed parameters (Sec. 2.2 "Per-voxel parameters", Sec. 2.5 constraints).
+template <int K>
+struct Vox {
+  float S0, dS0;      // softplus(s), sigmoid(s)
+  float f[K + 3];     // [csf, gm, wm_1..wm_K, res]
+  float d[K][3];      // unit fiber directions
+  float inrm[K];      // 1 / max(|v_k|, 1e-12)
+  float fin, omf;     // f_intra, 1 - f_intra
+};
+
+template <int K>
+__device__ __forceinline__ void load_theta(const float* __restrict__ theta, int Vp, int slot, bool act,
+                                           float (&th)[4 * K + 5]) {
+#pragma unroll
+  for (int q = 0; q < 4 * K + 5; ++q) th[q] = act ? theta[static_cast<size_t>(q) * Vp + slot] : 0.f;
+}
+
+template <int K>
+__device__ __forceinline__ void transform(const float (&th)[4 * K + 5], Vox<K>& P) {
+  constexpr int NF = K + 3;
+  P.S0 = softplusf_(th[0]);
+  P.dS0 = sigmoidf_(th[0]);
+  float mx = th[1];
+#pragma unroll
+  for (int i = 1; i < NF; ++i) mx = fmaxf(mx, th[1 + i]);
+  float sum = 0.f;
+#pragma unroll
+  for (int i = 0; i < NF; ++i) {
+    P.f[i] = expf(th[1 + i] - mx);
+    sum += P.f[i];
+  }
+  const float isum = 1.f / sum;
+#pragma unroll
+  for (int i = 0; i < NF; ++i) P.f[i] *= isum;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float vx = th[K + 4 + 3 * k], vy = th[K + 5 + 3 * k], vz = th[K + 6 + 3 * k];
+    const float n2 = fmaxf(vx * vx + vy * vy + vz * vz, kNormEps2);
+    const float in = rsqrtf(n2);
+    P.inrm[k] = in;
+    P.d[k][0] = vx * in;
+    P.d[k][1] = vy * in;
+    P.d[k][2] = vz * in;
+  }
+  P.fin = sigmoidf_(th[4 * K + 4]);
+  P.omf = 1.f - P.fin;
+}
+
+// Gradient w.r.t. transformed parameters -> raw parameters (adjoint of `transform`).
+template <int K>
+__device__ __forceinline__ void chain_raw(const Vox<K>& P, float gS0, const float (&gf)[K + 3],
+                                          const float (&gd)[K][3], float gfin, float (&g)[4 * K + 5]) {
+  constexpr int NF = K + 3;
+  g[0] = gS0 * P.dS0;
+  float dot = 0.f;
+#pragma unroll
+  for (int i = 0; i < NF; ++i) dot = fmaf(P.f[i], gf[i], dot);
+#pragma unroll
+  for (int i = 0; i < NF; ++i) g[1 + i] = P.f[i] * (gf[i] - dot);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float pd = gd[k][0] * P.d[k][0] + gd[k][1] * P.d[k][1] + gd[k][2] * P.d[k][2];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) g[K + 4 + 3 * k + c] = (gd[k][c] - pd * P.d[k][c]) * P.inrm[k];
+  }
+  g[4 * K + 4] = gfin * P.fin * P.omf;
+}
+
+// Writes the fractions and unit directions a neighbour needs (xf layout [4K+3][Vpad]).
+template <int K>
+__device__ __forceinline__ void store_xf(float* __restrict__ xf, int Vp, int slot, const Vox<K>& P) {
+#pragma unroll
+  for (int i = 0; i < K + 3; ++i) xf[static_cast<size_t>(i) * Vp + slot] = P.f[i];
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) xf[static_cast<size_t>(K + 3 + 3 * k + c) * Vp + slot] = P.d[k][c];
+}
+
+// Priors of Sec. 2.4 at one voxel: value, and gradient added to gf / gd (transformed space).
+// Repulsion and sparsity are local; the Huber-Laplacian uses the precomputed rho'(u)/|N|
+// of the voxel and its neighbours; directional continuity reads neighbour directions.
+template <int K>
+__device__ __forceinline__ float priors(const IterArgs& a, const Vox<K>& P, int slot, float inv_M,
+                                        const float* __restrict__ xf_cur, float (&gf)[K + 3],
+                                        float (&gd)[K][3]) {
+  constexpr int NF = K + 3;
+  const int Vp = a.Vpad;
+  float val = 0.f;
+  if (a.lam_rep > 0.f && K > 1) {
+    const float w = a.lam_rep * inv_M;
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+#pragma unroll
+      for (int j = i + 1; j < K; ++j) {
+        const float c = P.d[i][0] * P.d[j][0] + P.d[i][1] * P.d[j][1] + P.d[i][2] * P.d[j][2];
+        const float ac = fabsf(c);
+        const float fi = P.f[2 + i], fj = P.f[2 + j];
+        val = fmaf(w * fi * fj, ac, val);
+        gf[2 + i] = fmaf(w * fj, ac, gf[2 + i]);
+        gf[2 + j] = fmaf(w * fi, ac, gf[2 + j]);
+        const float sg = (c > 0.f) ? w * fi * fj : ((c < 0.f) ? -w * fi * fj : 0.f);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          gd[i][q] = fmaf(sg, P.d[j][q], gd[i][q]);
+          gd[j][q] = fmaf(sg, P.d[i][q], gd[j][q]);
+        }
+      }
+  }
+  if (a.lam_sparse > 0.f) {
+    const float w = a.lam_sparse * inv_M;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      if (P.f[2 + k] < a.tau) {
+        val = fmaf(w, P.f[2 + k], val);
+        gf[2 + k] += w;
+      }
+  }
+  if (a.nb_priors) {
+    const uint32_t fl = a.vflag[slot];
+    const int ncnt = (fl >> 8) & 15;
+    if (ncnt > 0) {
+      int nb[6];
+#pragma unroll
+      for (int e = 0; e < 6; ++e) nb[e] = a.nbr[static_cast<size_t>(e) * Vp + slot];
+      if (a.lam_sp > 0.f) {
+        const float w = a.lam_sp * inv_M;
+        val += a.lp[slot];
+#pragma unroll
+        for (int c = 0; c < NF; ++c) {
+          const float* hc = a.hsp + static_cast<size_t>(c) * Vp;
+          float s = hc[slot] * static_cast<float>(ncnt);
+#pragma unroll
+          for (int e = 0; e < 6; ++e)
+            if (nb[e] >= 0) s -= hc[nb[e]];
+          gf[c] = fmaf(w, s, gf[c]);
+        }
+      }
+      if (a.lam_dir > 0.f) {
+        const float w = a.lam_dir * inv_M;
+        const float inv_n = 1.f / static_cast<float>(ncnt);
+#pragma unroll
+        for (int e = 0; e < 6; ++e) {
+          const int x = nb[e];
+          if (x < 0) continue;
+          const int nx_cnt = (a.vflag[x] >> 8) & 15;
+          const float wgt = inv_n + 1.f / static_cast<float>(nx_cnt);
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            float dx[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) dx[q] = xf_cur[static_cast<size_t>(K + 3 + 3 * k + q) * Vp + x];
+            const float c = P.d[k][0] * dx[0] + P.d[k][1] * dx[1] + P.d[k][2] * dx[2];
+            val = fmaf(w * inv_n, 1.f - c * c, val);
+            const float s = -2.f * w * c * wgt;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) gd[k][q] = fmaf(s, dx[q], gd[k][q]);
+          }
+        }
+      }
+    }
+  }
+  return val;
+}
+
+// Total-variation term of the upsampled bias field at voxel (x, y, z) (reading R11):
+// forward pairs inside the mask count once; returns the value and adds dTV/dU(x) to gU.
+__device__ __forceinline__ float tv_term(const float* blr, int x, int y, int z, const GroupDev& gr,
+                                         uint32_t fl, float B0, float w, float eps, float& gU) {
+  float val = 0.f;
+  const int off[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    if (fl & (1u << (2 * ax))) {   // x + e masked
+      const TriW t = tri_weights(x + off[ax][0], y + off[ax][1], z + off[ax][2], gr.nx, gr.ny, gr.nz);
+      const float B1 = expf(tri_eval(blr, t));
+      const float dB = B1 - B0;
+      const float sq = sqrtf(dB * dB + eps);
+      val = fmaf(w, sq, val);
+      gU = fmaf(-w * dB / sq, B0, gU);
+    }
+    if (fl & (2u << (2 * ax))) {   // x - e masked
+      const TriW t = tri_weights(x - off[ax][0], y - off[ax][1], z - off[ax][2], gr.nx, gr.ny, gr.nz);
+      const float Bm = expf(tri_eval(blr, t));
+      const float dB = B0 - Bm;
+      const float sq = sqrtf(dB * dB + eps);
+      gU = fmaf(w * dB / sq, B0, gU);
+    }
+  }
+  return val;
+}
+
+// Voxel-level gradient accumulators of the data term (unscaled), per thread.
+template <int K>
+struct Acc {
+  float gS0, gcsf, ggm, gres, gin;
+  float gw[K];
+  float gd[K][3];
+  float l1, l2, l3;   // MSE: sum r^2 | NLL: sum (y-|yh|)^2, sum |y yh| Q, sum L
+  float u;            // sum_n r A B S (= dJ/dU unscaled, calibration)
+};
+
+template <int K>
+__device__ __forceinline__ void acc_zero(Acc<K>& A) {
+  A.gS0 = A.gcsf = A.ggm = A.gres = A.gin = 0.f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    A.gw[k] = 0.f;
+    A.gd[k][0] = A.gd[k][1] = A.gd[k][2] = 0.f;
+  }
+  A.l1 = A.l2 = A.l3 = A.u = 0.f;
+}
+
+template <int K, int TPV>
+__device__ __forceinline__ void acc_reduce_tpv(Acc<K>& A) {
+  if constexpr (TPV > 1) {
+    A.gS0 = warp_sum_range<1, TPV / 2>(A.gS0);
+    A.gcsf = warp_sum_range<1, TPV / 2>(A.gcsf);
+    A.ggm = warp_sum_range<1, TPV / 2>(A.ggm);
+    A.gres = warp_sum_range<1, TPV / 2>(A.gres);
+    A.gin = warp_sum_range<1, TPV / 2>(A.gin);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      A.gw[k] = warp_sum_range<1, TPV / 2>(A.gw[k]);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) A.gd[k][c] = warp_sum_range<1, TPV / 2>(A.gd[k][c]);
+    }
+    A.l1 = warp_sum_range<1, TPV / 2>(A.l1);
+    A.l2 = warp_sum_range<1, TPV / 2>(A.l2);
+    A.l3 = warp_sum_range<1, TPV / 2>(A.l3);
+    A.u = warp_sum_range<1, TPV / 2>(A.u);
+  }
+}
+
+// One (voxel, measurement) pair: forward model (Eqs. 2-5), data-term derivative, and
+// accumulation of the adjoint. `rr_ext` (>= -inf) replaces the residual derivative when
+// the caller supplies dL/dy_hat (plain adjoint); returns the unscaled u = r A B S.
+template <int K, int LOSS, bool CAL, bool EXT_R>
+__device__ __forceinline__ void pair(const Vox<K>& P, const MeasRow& R, float yv, float B, float inv_s2,
+                                     float r_ext, Acc<K>& A, float& rr_out, float& u_out) {
+  float T = P.f[0] * R.ecsf;
+  T = fmaf(P.f[1], R.egm, T);
+  T = fmaf(P.f[K + 2], R.eres, T);
+  float E[K], e1[K], p[K], c[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    c[k] = fmaf(P.d[k][0], R.gx, fmaf(P.d[k][1], R.gy, P.d[k][2] * R.gz));
+    const float c2 = c[k] * c[k];
+    e1[k] = ex2f_(-R.kpar * c2);
+    const float e2 = ex2f_(fmaf(R.kperp, c2, -R.kperp));
+    p[k] = e1[k] * e2;
+    E[k] = fmaf(P.fin, e1[k], P.omf * p[k]);
+    T = fmaf(P.f[2 + k], E[k], T);
+  }
+  const float S = P.S0 * T;
+  float yh, AB = 1.f;
+  if (CAL) {
+    AB = R.A * B;
+    yh = fmaf(AB, S, R.beta);
+  } else {
+    yh = S;
+  }
+  float rr;
+  if (EXT_R) {
+    rr = r_ext;
+  } else if (LOSS == kLossMSE) {
+    rr = yh - yv;
+    A.l1 = fmaf(rr, rr, A.l1);
+  } else {
+    const float ay = fabsf(yh);
+    const float sy = (yh >= 0.f) ? yv : -yv;
+    float Qz, Lz;
+    bessel_QL<true>(yv * ay * inv_s2, Qz, Lz);
+    const float e = yv - ay;
+    A.l1 = fmaf(e, e, A.l1);
+    A.l2 = fmaf(yv * ay, Qz, A.l2);
+    A.l3 += Lz;
+    rr = fmaf(sy, Qz, yh - sy);      // y_hat - y R(z), R = I1/I0
+  }
+  rr_out = rr;
+  const float q = CAL ? rr * AB : rr;   // dJ/dS (unscaled)
+  if (CAL) {
+    u_out = q * S;
+    A.u += u_out;
+  }
+  A.gS0 = fmaf(q, T, A.gS0);
+  A.gcsf = fmaf(q, R.ecsf, A.gcsf);
+  A.ggm = fmaf(q, R.egm, A.ggm);
+  A.gres = fmaf(q, R.eres, A.gres);
+  const float cperp = R.dperp2 * P.omf;
+  float gin = 0.f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    A.gw[k] = fmaf(q, E[k], A.gw[k]);
+    gin = fmaf(P.f[2 + k], e1[k] - p[k], gin);
+    const float dE = c[k] * fmaf(-R.dpar2, E[k], cperp * p[k]);   // dE_wm/dc
+    const float w = q * dE;
+    A.gd[k][0] = fmaf(w, R.gx, A.gd[k][0]);
+    A.gd[k][1] = fmaf(w, R.gy, A.gd[k][1]);
+    A.gd[k][2] = fmaf(w, R.gz, A.gd[k][2]);
+  }
+  A.gin = fmaf(q, gin, A.gin);
+}
+
+// Scaled data-term gradient w.r.t. transformed parameters.
+template <int K>
+__device__ __forceinline__ void data_grad(const Vox<K>& P, const Acc<K>& A, float scale, float& gS0,
+                                          float (&gf)[K + 3], float (&gd)[K][3], float& gfin) {
+  const float sS = scale * P.S0;
+  gS0 = A.gS0 * scale;
+  gf[0] = A.gcsf * sS;
+  gf[1] = A.ggm * sS;
+  gf[K + 2] = A.gres * sS;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    gf[2 + k] = A.gw[k] * sS;
+    const float w = sS * P.f[2 + k];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) gd[k][c] = A.gd[k][c] * w;
+  }
+  gfin = A.gin * sS;
+}
+
+__device__ __forceinline__ void block_reduce3(double v0, double v1, double v2, double (*s_red)[3],
+                                              double* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v0 = warp_sum_d(v0);
+  v1 = warp_sum_d(v1);
+  v2 = warp_sum_d(v2);
+  if (lane == 0) {
+    s_red[warp][0] = v0;
+    s_red[warp][1] = v1;
+    s_red[warp][2] = v2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0, c = 0;
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) {
+      a += s_red[w][0];
+      b += s_red[w][1];
+      c += s_red[w][2];
+    }
+    out[0] = a;
+    out[1] = b;
+    out[2] = c;
+  }
+}
+
+// ===========================================================================
+// Fused iteration: one persistent kernel over the tile queue does synthesis,
+// calibration, data term, adjoint, priors, chain rule and the voxel Adam update.
+// ===========================================================================
+template <int K, int TPV, int LOSS, bool CAL>
+__global__ void __launch_bounds__(256) k_iter_fused(const IterArgs a) {
+  constexpr int NF = K + 3, Q = 4 * K + 5, XF = 4 * K + 3;
+  extern __shared__ __align__(16) unsigned char smem[];
+  MeasRow* s_tab = reinterpret_cast<MeasRow*>(smem);
+  float* s_blr = reinterpret_cast<float*>(s_tab + a.Nmax);
+  float* s_ab = s_blr + (CAL ? kNGrid : 0);
+  __shared__ uint64_t s_bar;
+  __shared__ int s_tile;
+  __shared__ double s_red[8][3];
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int vl = tid / TPV, js = tid % TPV;
+  const int TV = a.TV, Vp = a.Vpad;
+  const int step = *a.step;
+  const int par = step & 1;
+  const float* xf_cur = a.xf + static_cast<size_t>(par) * XF * Vp;
+  float* xf_nxt = a.xf + static_cast<size_t>(par ^ 1) * XF * Vp;
+  if (tid == 0) {
+    mbar_init(&s_bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const float stepsz = a.adamc[0], isbc2 = a.adamc[1];
+  int cur_group = -1;
+  uint32_t phase = 0;
+  bool failed = false;
+
+  for (;;) {
+    if (tid == 0) s_tile = atomicAdd(a.queue, 1);
+    __syncthreads();
+    const int t = s_tile;
+    if (t >= a.ntiles) break;
+    const Tile tl = a.tiles[t];
+    const GroupDev gr = a.groups[tl.group];
+    const int N = tl.n_meas;
+    if (tl.group != cur_group) {
+      if (tid == 0) {
+        fence_proxy_async_smem();
+        const uint32_t tb = static_cast<uint32_t>(N * sizeof(MeasRow));
+        mbar_expect_tx(&s_bar, tb + (CAL ? kNGrid * 4u : 0u));
+        tma_bulk_g2s(s_tab, a.table + gr.table_off, tb, &s_bar);
+        if (CAL) tma_bulk_g2s(s_blr, a.gparams + gr.gp_off + 4 + 2 * gr.N4, kNGrid * 4u, &s_bar);
+      }
+      const bool ok_wait = mbar_wait(&s_bar, phase);
+      if (__syncthreads_or(!ok_wait)) {   // block-uniform decision
+        if (tid == 0) atomicOr(a.status, kStTimeout);
+        mbar_wait(&s_bar, phase);   // let an in-flight copy land before leaving
+        failed = true;
+        break;
+      }
+      phase ^= 1;
+      cur_group = tl.group;
+    }
+    const int slot = tl.slot0 + vl;
+    const bool act = vl < tl.count;
+    float th[Q];
+    load_theta<K>(a.theta, Vp, slot, act, th);
+    Vox<K> P;
+    transform<K>(th, P);
+    float inv_s2 = 0.f, slog = 0.f;
+    if (LOSS == kLossNLL) {
+      slog = a.gparams[gr.gp_off];
+      inv_s2 = expf(-2.f * slog);
+    }
+    const float scale = (LOSS == kLossMSE) ? 2.f * gr.inv_M : inv_s2;
+    float B = 1.f;
+    int cx = 0, cy = 0, cz = 0;
+    if (CAL) {
+      unpack_coord(act ? a.vcoord[slot] : 0u, cx, cy, cz);
+      B = expf(tri_eval(s_blr, tri_weights(cx, cy, cz, gr.nx, gr.ny, gr.nz)));
+    }
+    Acc<K> A;
+    acc_zero<K>(A);
+    const float* __restrict__ yt = a.y + tl.y_off;
+    const int iters = (N + TPV - 1) / TPV;
+#pragma unroll 2
+    for (int i = 0; i < iters; ++i) {
+      const int n = i * TPV + js;
+      const bool ok = act && (n < N);
+      float rr = 0.f, u = 0.f;
+      if (ok) {
+        const MeasRow R = s_tab[n];
+        const float yv = __ldg(yt + static_cast<size_t>(n) * TV + vl);
+        pair<K, LOSS, CAL, false>(P, R, yv, B, inv_s2, 0.f, A, rr, u);
+      }
+      if (CAL) {
+        float su = warp_sum_range<TPV, 16>(ok ? u : 0.f);
+        float sr = warp_sum_range<TPV, 16>(ok ? rr : 0.f);
+        if (lane < TPV && n < N) {
+          s_ab[(warp * 2) * a.Nmax + n] = su;
+          s_ab[(warp * 2 + 1) * a.Nmax + n] = sr;
+        }
+      }
+    }
+    acc_reduce_tpv<K, TPV>(A);
+
+    // ---- data-term gradient and value
+    float gS0, gf[NF], gd[K][3], gfin;
+    data_grad<K>(P, A, scale, gS0, gf, gd, gfin);
+    float dloss, dsig = 0.f;
+    if (LOSS == kLossMSE) {
+      dloss = A.l1 * gr.inv_M;
+    } else {
+      dloss = 2.f * slog * N + 0.5f * inv_s2 * A.l1 - A.l3;
+      dsig = 2.f * N - inv_s2 * (A.l1 + 2.f * A.l2);
+    }
+    // ---- priors
+    float ploss = priors<K>(a, P, slot, gr.inv_M, xf_cur, gf, gd);
+    float gUv = A.u * scale;
+    if (CAL && a.w_tv > 0.f) {
+      const uint32_t fl = act ? a.vflag[slot] : 0u;
+      ploss += tv_term(s_blr, cx, cy, cz, gr, fl, B, a.w_tv * gr.inv_M, a.tv_eps, gUv);
+    }
+    // ---- chain rule and Adam
+    float g[Q];
+    chain_raw<K>(P, gS0, gf, gd, gfin, g);
+    const bool writer = act && (js == 0);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const size_t ix = static_cast<size_t>(q) * Vp + slot;
+      float mq = writer ? a.m[ix] : 0.f;
+      float vq = writer ? a.v[ix] : 0.f;
+      mq = fmaf(a.beta1, mq, (1.f - a.beta1) * g[q]);
+      vq = fmaf(a.beta2, vq, (1.f - a.beta2) * g[q] * g[q]);
+      th[q] -= stepsz * mq / fmaf(sqrtf(vq), isbc2, a.eps);
+      if (writer) {
+        a.m[ix] = mq;
+        a.v[ix] = vq;
+        a.theta[ix] = th[q];
+      }
+    }
+    if (a.nb_priors && writer) {
+      Vox<K> Pn;
+      transform<K>(th, Pn);
+      store_xf<K>(xf_nxt, Vp, slot, Pn);
+    }
+    if (CAL && writer) a.gU[slot] = gUv;
+    // ---- tile partials (fixed-order reductions)
+    block_reduce3(writer ? static_cast<double>(dloss) : 0.0, writer ? static_cast<double>(dsig) : 0.0,
+                  writer ? static_cast<double>(ploss) : 0.0, s_red, a.tile_red + 4 * static_cast<size_t>(t));
+    if (CAL) {
+      // s_ab complete after block_reduce3's barrier
+      const int NW = blockDim.x >> 5;
+      for (int e = tid; e < 2 * N; e += blockDim.x) {
+        const int w2 = (e < N) ? 0 : 1;
+        const int n = e - w2 * N;
+        float s = 0.f;
+        for (int w = 0; w < NW; ++w) s += s_ab[(w * 2 + w2) * a.Nmax + n];
+        a.tile_ab[tl.ab_off + e] = s * scale;
+      }
+    }
+    __syncthreads();
+  }
+  (void)failed;
+  // The last CTA to leave resets the queue for the next iteration.
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(a.done, 1) == static_cast<int>(gridDim.x) - 1) {
+      *a.queue = 0;
+      *a.done = 0;
+      __threadfence();
+    }
+  }
+}
+
+// ===========================================================================
+// Plain (unfused) kernels: one launch per step and per patch (tile range).
+// ===========================================================================
+
+// Fractions and unit directions for a tile range (slot-parallel).
+template <int K>
+__global__ void k_transform(const IterArgs a, int tile_begin, int tile_end) {
+  const int XF = 4 * K + 3;
+  const int slot = tile_begin * a.TV + blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= tile_end * a.TV) return;
+  const Tile tl = a.tiles[slot / a.TV];
+  if (slot - tl.slot0 >= tl.count) return;
+  float th[4 * K + 5];
+  load_theta<K>(a.theta, a.Vpad, slot, true, th);
+  Vox<K> P;
+  transform<K>(th, P);
+  store_xf<K>(a.xf + static_cast<size_t>((*a.step) & 1) * XF * a.Vpad, a.Vpad, slot, P);
+}
+
+// Synthesis + calibration: y_hat for every (voxel, measurement) of the tile range.
+template <int K, int TPV, bool CAL>
+__global__ void __launch_bounds__(256) k_synth(const IterArgs a, const PlainArgs pa) {
+  const int t = pa.tile_begin + blockIdx.x;
+  if (t >= pa.tile_end) return;
+  const Tile tl = a.tiles[t];
+  const GroupDev gr = a.groups[tl.group];
+  const MeasRow* tab = a.table + gr.table_off;
+  const int vl = threadIdx.x / TPV, js = threadIdx.x % TPV;
+  if (vl >= tl.count) return;
+  const int slot = tl.slot0 + vl;
+  float th[4 * K + 5];
+  load_theta<K>(a.theta, a.Vpad, slot, true, th);
+  Vox<K> P;
+  transform<K>(th, P);
+  float B = 1.f;
+  if (CAL) {
+    int x, y, z;
+    unpack_coord(a.vcoord[slot], x, y, z);
+    B = expf(tri_eval(a.gparams + gr.gp_off + 4 + 2 * gr.N4, tri_weights(x, y, z, gr.nx, gr.ny, gr.nz)));
+  }
+  for (int n = js; n < tl.n_meas; n += TPV) {
+    const MeasRow R = tab[n];
+    float T = P.f[0] * R.ecsf;
+    T = fmaf(P.f[1], R.egm, T);
+    T = fmaf(P.f[K + 2], R.eres, T);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const float c = fmaf(P.d[k][0], R.gx, fmaf(P.d[k][1], R.gy, P.d[k][2] * R.gz));
+      const float c2 = c * c;
+      const float e1 = ex2f_(-R.kpar * c2);
+      const float e2 = ex2f_(fmaf(R.kperp, c2, -R.kperp));
+      T = fmaf(P.f[2 + k], fmaf(P.fin, e1, P.omf * e1 * e2), T);
+    }
+    const float S = P.S0 * T;
+    pa.yhat[tl.y_off + static_cast<size_t>(n) * a.TV + vl] = CAL ? fmaf(R.A * B, S, R.beta) : S;
+  }
+}
+
+// Data term: per-element derivative dL/dy_hat (scaled) and per-tile loss / sigma partials.
+template <int LOSS>
+__global__ void __launch_bounds__(256) k_loss(const IterArgs a, const PlainArgs pa) {
+  __shared__ double s_red[8][3];
+  const int t = pa.tile_begin + blockIdx.x;
+  if (t >= pa.tile_end) return;
+  const Tile tl = a.tiles[t];
+  const GroupDev gr = a.groups[tl.group];
+  const int N = tl.n_meas;
+  float inv_s2 = 0.f, slog = 0.f;
+  if (LOSS == kLossNLL) {
+    slog = a.gparams[gr.gp_off];
+    inv_s2 = expf(-2.f * slog);
+  }
+  const float scale = (LOSS == kLossMSE) ? 2.f * gr.inv_M : inv_s2;
+  double l = 0.0, sg = 0.0;
+  for (int e = threadIdx.x; e < N * a.TV; e += blockDim.x) {
+    const int n = e / a.TV, vl = e - n * a.TV;
+    if (vl >= tl.count) continue;
+    const size_t ix = tl.y_off + e;
+    const float yh = pa.yhat[ix], yv = a.y[ix];
+    float rr;
+    if (LOSS == kLossMSE) {
+      rr = yh - yv;
+      l += static_cast<double>(rr * rr) * gr.inv_M;
+    } else {
+      const float ay = fabsf(yh);
+      const float sy = (yh >= 0.f) ? yv : -yv;
+      float Qz, Lz;
+      bessel_QL<true>(yv * ay * inv_s2, Qz, Lz);
+      const float d = yv - ay;
+      l += static_cast<double>(2.f * slog + 0.5f * inv_s2 * d * d - Lz);
+      sg += static_cast<double>(2.f - inv_s2 * (d * d + 2.f * yv * ay * Qz));
+      rr = fmaf(sy, Qz, yh - sy);
+    }
+    pa.r[ix] = rr * scale;
+  }
+  double out[3];
+  block_reduce3(l, sg, 0.0, s_red, out);
+  if (threadIdx.x == 0) {
+    a.tile_red[4 * static_cast<size_t>(t) + 0] = out[0];
+    a.tile_red[4 * static_cast<size_t>(t) + 1] = out[1];
+  }
+}
+
+// Adjoint: recomputes the compartment exponentials and back-substitutes the stored
+// dL/dy_hat into raw-parameter gradients, alpha/beta partials and dJ/dU.
+template <int K, int TPV, bool CAL>
+__global__ void __launch_bounds__(256) k_adjoint(const IterArgs a, const PlainArgs pa) {
+  constexpr int NF = K + 3, Q = 4 * K + 5;
+  extern __shared__ __align__(16) unsigned char smem[];
+  float* s_ab = reinterpret_cast<float*>(smem);   // [NW][2][Nmax]
+  const int t = pa.tile_begin + blockIdx.x;
+  if (t >= pa.tile_end) return;
+  const Tile tl = a.tiles[t];
+  const GroupDev gr = a.groups[tl.group];
+  const MeasRow* tab = a.table + gr.table_off;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int vl = tid / TPV, js = tid % TPV;
+  const bool act = vl < tl.count;
+  const int slot = tl.slot0 + vl;
+  const int N = tl.n_meas;
+  float th[Q];
+  load_theta<K>(a.theta, a.Vpad, slot, act, th);
+  Vox<K> P;
+  transform<K>(th, P);
+  float B = 1.f;
+  if (CAL) {
+    int x, y, z;
+    unpack_coord(act ? a.vcoord[slot] : 0u, x, y, z);
+    B = expf(tri_eval(a.gparams + gr.gp_off + 4 + 2 * gr.N4, tri_weights(x, y, z, gr.nx, gr.ny, gr.nz)));
+  }
+  Acc<K> A;
+  acc_zero<K>(A);
+  const int iters = (N + TPV - 1) / TPV;
+  for (int i = 0; i < iters; ++i) {
+    const int n = i * TPV + js;
+    const bool ok = act && (n < N);
+    float rr = 0.f, u = 0.f;
+    if (ok) {
+      const size_t ix = tl.y_off + static_cast<size_t>(n) * a.TV + vl;
+      pair<K, kLossMSE, CAL, true>(P, tab[n], 0.f, B, 0.f, pa.r[ix], A, rr, u);
+    }
+    if (CAL) {
+      float su = warp_sum_range<TPV, 16>(ok ? u : 0.f);
+      float sr = warp_sum_range<TPV, 16>(ok ? rr : 0.f);
+      if (lane < TPV && n < N) {
+        s_ab[(warp * 2) * a.Nmax + n] = su;
+        s_ab[(warp * 2 + 1) * a.Nmax + n] = sr;
+      }
+    }
+  }
+  acc_reduce_tpv<K, TPV>(A);
+  float gS0, gf[NF], gd[K][3], gfin;
+  data_grad<K>(P, A, 1.f, gS0, gf, gd, gfin);   // r already scaled
+  float g[Q];
+  chain_raw<K>(P, gS0, gf, gd, gfin, g);
+  if (act && js == 0) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) pa.grad[static_cast<size_t>(q) * a.Vpad + slot] = g[q];
+    if (CAL) a.gU[slot] = A.u;
+  }
+  if (CAL) {
+    __syncthreads();
+    const int NW = blockDim.x >> 5;
+    for (int e = tid; e < 2 * N; e += blockDim.x) {
+      const int w2 = (e < N) ? 0 : 1;
+      const int n = e - w2 * N;
+      float s = 0.f;
+      for (int w = 0; w < NW; ++w) s += s_ab[(w * 2 + w2) * a.Nmax + n];
+      a.tile_ab[tl.ab_off + e] = s;
+    }
+  }
+}
+
+// Huber-Laplacian preparation: rho'(u_c(x)) / |N(x)| and the prior value per voxel (Eq. 6).
+template <int K>
+__global__ void k_prior_prep(const IterArgs a, int tile_begin, int tile_end) {
+  constexpr int NF = K + 3, XF = 4 * K + 3;
+  const int slot = tile_begin * a.TV + blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= tile_end * a.TV) return;
+  const Tile tl = a.tiles[slot / a.TV];
+  if (slot - tl.slot0 >= tl.count) return;
+  const GroupDev gr = a.groups[tl.group];
+  const int Vp = a.Vpad;
+  const float* xf = a.xf + static_cast<size_t>((*a.step) & 1) * XF * Vp;
+  const int ncnt = (a.vflag[slot] >> 8) & 15;
+  float val = 0.f;
+  if (ncnt == 0) {
+    for (int c = 0; c < NF; ++c) a.hsp[static_cast<size_t>(c) * Vp + slot] = 0.f;
+  } else {
+    int nb[6];
+    for (int e = 0; e < 6; ++e) nb[e] = a.nbr[static_cast<size_t>(e) * Vp + slot];
+    const float inv_n = 1.f / static_cast<float>(ncnt);
+    for (int c = 0; c < NF; ++c) {
+      const float* fc = xf + static_cast<size_t>(c) * Vp;
+      float s = 0.f;
+      for (int e = 0; e < 6; ++e)
+        if (nb[e] >= 0) s += fc[nb[e]];
+      const float u = fc[slot] - s * inv_n;
+      val += huber_rho(u, a.huber_delta);
+      a.hsp[static_cast<size_t>(c) * Vp + slot] = huber_drho(u, a.huber_delta) * inv_n;
+    }
+  }
+  a.lp[slot] = a.lam_sp * gr.inv_M * val;
+}
+
+// Priors (and the bias-field TV term) for a tile range: value into the tile's prior
+// slot (mode bit 0) and chain-ruled gradient added to `grad` / gU (mode bit 1).
+template <int K>
+__global__ void __launch_bounds__(256) k_prior(const IterArgs a, const PlainArgs pa) {
+  constexpr int NF = K + 3, Q = 4 * K + 5, XF = 4 * K + 3;
+  __shared__ double s_red[8][3];
+  const int t = pa.tile_begin + blockIdx.y;
+  if (t >= pa.tile_end) return;
+  const Tile tl = a.tiles[t];
+  const GroupDev gr = a.groups[tl.group];
+  const int vl = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool act = vl < tl.count;
+  const int slot = tl.slot0 + vl;
+  const float* xf_cur = a.xf + static_cast<size_t>((*a.step) & 1) * XF * a.Vpad;
+  float th[Q];
+  load_theta<K>(a.theta, a.Vpad, slot, act, th);
+  Vox<K> P;
+  transform<K>(th, P);
+  float gf[NF], gd[K][3];
+#pragma unroll
+  for (int i = 0; i < NF; ++i) gf[i] = 0.f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) gd[k][0] = gd[k][1] = gd[k][2] = 0.f;
+  float val = 0.f;
+  if (act) {
+    val = priors<K>(a, P, slot, gr.inv_M, xf_cur, gf, gd);
+    if (gr.calib && a.w_tv > 0.f) {
+      int x, y, z;
+      unpack_coord(a.vcoord[slot], x, y, z);
+      const float* blr = a.gparams + gr.gp_off + 4 + 2 * gr.N4;
+      const float B0 = expf(tri_eval(blr, tri_weights(x, y, z, gr.nx, gr.ny, gr.nz)));
+      float gUtv = 0.f;
+      val += tv_term(blr, x, y, z, gr, a.vflag[slot], B0, a.w_tv * gr.inv_M, a.tv_eps, gUtv);
+      if (pa.mode & 2) a.gU[slot] += gUtv;
+    }
+    if (pa.mode & 2) {
+      float g[Q];
+      chain_raw<K>(P, 0.f, gf, gd, 0.f, g);
+#pragma unroll
+      for (int q = 0; q < Q; ++q) pa.grad[static_cast<size_t>(q) * a.Vpad + slot] += g[q];
+    }
+  }
+  if (pa.mode & 1) {
+    // one value per (tile, x-block): the launch uses a single x-block per tile
+    double out[3];
+    block_reduce3(static_cast<double>(val), 0.0, 0.0, s_red, out);
+    if (threadIdx.x == 0) a.tile_red[4 * static_cast<size_t>(t) + 2] = out[0];
+  }
+}
+
+}  // namespace prism

@@ -1,0 +1,176 @@
+"""GPU parity: the CUDA library (through the C-ABI) against the FP64 oracle.
+
+Element-wise y_hat, objective per group, gradient per parameter block, one Adam
+step (fused and plain paths), and a 200-iteration fit of the one-patch crossing
+workload. Sizes span several tiles with ragged tails.
+"""
+import numpy as np
+import pytest
+import torch
+
+import phantoms as P
+from oracle import metrics as M
+from oracle import prism_oracle as O
+from tests.helpers import (TOL_GRAD, TOL_LOSS, TOL_SIGNAL, block_slices, inits_for, make_pair, normwise,
+                           signal_rel, split_groups)
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    # loss, calibration, K, threads per voxel, extra options
+    ("mse", False, 3, 1, dict(lam_sp=0.01, lam_dir=0.005)),
+    ("mse", False, 3, 4, dict(lam_sp=0.01, lam_dir=0.005)),
+    ("mse", False, 3, 16, dict()),
+    ("nll", False, 2, 1, dict()),
+    ("nll", False, 3, 4, dict(lam_sp=0.01)),
+    ("mse", True, 3, 1, dict(lam_dir=0.005)),
+    ("nll", True, 3, 1, dict(lam_sp=0.01, lam_dir=0.005)),
+    ("nll", True, 2, 16, dict()),
+    ("mse", False, 1, 1, dict()),
+    ("mse", False, 5, 4, dict(lam_sp=0.01)),
+]
+
+
+def _problem(cal, seed=0, nvol=2):
+    sch = P.make_scheme(3, [(1000, 14), (2500, 15)], seed)       # N = 32
+    sch2 = P.make_scheme(2, [(800, 9), (2000, 10)], seed + 1)    # N = 21
+    vols = [P.random_volume((7, 5, 6), scheme=sch, seed=seed, mask_density=0.75, calibration=cal)]
+    if nvol > 1:
+        vols.append(P.random_volume((5, 6, 4), scheme=sch2, seed=seed + 1, mask_density=0.6, calibration=cal))
+    return vols
+
+
+def _perturb_groups(f, rng, cal, loss):
+    packed = f.groups().copy()
+    for gi, g in enumerate(f.group_view(packed)):
+        off = f.group_layout()
+        a, b, c, d = (int(x) for x in off[4 * gi:4 * gi + 4])
+        N = f.n_meas[gi]
+        if loss == "nll":
+            packed[a] = np.log(0.05 + 0.02 * gi)
+        if cal:
+            packed[b:b + N] = rng.normal(0, 0.05, N)
+            packed[c:c + N] = rng.normal(0, 0.02, N)
+            packed[d:d + 512] = rng.normal(0, 0.1, 512)
+    f.set_groups(packed)
+    return packed
+
+
+@pytest.mark.parametrize("loss,cal,K,tpv,extra", CASES)
+def test_forward_and_gradient(loss, cal, K, tpv, extra):
+    rng = np.random.default_rng(1)
+    vols = _problem(cal)
+    inits = [th + rng.normal(0, 0.3, th.shape).astype(np.float32) for th in inits_for(vols, K, 3)]
+    kw = dict(K=K, loss=loss, calibration=cal, patch_dim=4, threads_per_voxel=tpv, **extra)
+    f, ovs = make_pair(vols, inits, **kw)
+    packed = _perturb_groups(f, rng, cal, loss)
+    gps = split_groups(packed, f)
+    loss_g, yhat = f.forward(want_yhat=True)
+    gth, gg = f.backward()
+    torch.cuda.synchronize()
+    yhat = yhat.cpu().numpy()
+    gth = gth.cpu().numpy()
+    gg = gg.cpu().numpy()
+    off = f.group_layout()
+    pos = 0
+    vpos = 0
+    for gi, ov in enumerate(ovs):
+        th = torch.as_tensor(inits[gi]).double()
+        yref, _ = O.predict(ov, th, gps[gi])
+        n = ov.n_vox * ov.n_meas
+        assert signal_rel(yhat[pos:pos + n].reshape(ov.n_vox, ov.n_meas), yref.numpy()) <= TOL_SIGNAL
+        pos += n
+        J, parts, g, ggr = O.value_and_grad(ov, th, gps[gi])
+        assert abs(float(loss_g[gi]) - float(J)) <= TOL_LOSS * abs(float(J)), (gi, float(loss_g[gi]), float(J), parts)
+        gv = gth[vpos:vpos + ov.n_vox]
+        vpos += ov.n_vox
+        for name, sl in block_slices(K).items():
+            e = normwise(gv[:, sl], g[:, sl].numpy())
+            assert e <= TOL_GRAD, (gi, name, e)
+        a, b, c, d = (int(x) for x in off[4 * gi:4 * gi + 4])
+        N = ov.n_meas
+        if loss == "nll":
+            e = normwise([gg[a]], [float(ggr["sigma_log"])])
+            assert e <= TOL_GRAD, ("sigma", e, gg[a], float(ggr["sigma_log"]))
+        if cal:
+            assert normwise(gg[b:b + N], ggr["alpha"].numpy()) <= TOL_GRAD
+            assert normwise(gg[c:c + N], ggr["beta"].numpy()) <= TOL_GRAD
+            assert normwise(gg[d:d + 512], ggr["blr"].numpy().ravel()) <= TOL_GRAD
+    f.close()
+
+
+@pytest.mark.parametrize("fused", [1, 0])
+@pytest.mark.parametrize("loss,cal", [("mse", False), ("nll", True)])
+def test_adam_steps_match_oracle(fused, loss, cal):
+    """Three iterations (objective, gradient, Adam) on the fused and the plain path."""
+    vols = _problem(cal)
+    K = 3
+    inits = inits_for(vols, K, 5)
+    kw = dict(K=K, loss=loss, calibration=cal, patch_dim=4, lam_sp=0.01, lam_dir=0.005, fused=fused,
+              use_graph=fused)
+    f, ovs = make_pair(vols, inits, **kw)
+    f.step(3)
+    f.sync()
+    th = f.params_host()
+    res = O.fit(ovs, [torch.as_tensor(t).double() for t in inits], 3)
+    hist = f.loss_history()
+    np.testing.assert_allclose(hist, res.loss_history, rtol=1e-5)
+    ref = np.concatenate([t.numpy() for t in res.theta])
+    # each Adam step moves a parameter by ~lr; three steps agree to float32 rounding
+    assert float(np.max(np.abs(th - ref))) < 3e-4
+    f.close()
+
+
+def test_fit_crossing_patch_200_iterations():
+    """One 8^3 patch of crossings, 96 measurements, MSE, 200 Adam iterations: median
+    matched angular deviation <= 0.5 deg and identical peak counts per voxel."""
+    vol = P.crossing_patch(0)
+    K = 3
+    th0 = P.default_init(vol.n_vox, K, 0)
+    f, ovs = make_pair([vol], [th0], K=K, patch_dim=8)
+    f.step(200)
+    f.sync()
+    th_gpu = f.params_host()
+    res = O.fit(ovs, [torch.as_tensor(th0).double()], 200)
+    dev, pa, pb = M.matched_deviation(res.theta[0].numpy(), th_gpu, K)
+    assert float(np.median(dev)) <= 0.5, float(np.median(dev))
+    assert np.array_equal(pa, pb), int(np.sum(pa != pb))
+    np.testing.assert_allclose(f.loss_history()[:, 0], res.loss_history[:, 0], rtol=1e-3)
+    f.close()
+
+
+def test_fused_is_deterministic_and_resumable():
+    vols = _problem(True)
+    K = 3
+    inits = inits_for(vols, K, 9)
+    kw = dict(K=K, loss="nll", calibration=True, patch_dim=4, lam_sp=0.01, lam_dir=0.005)
+    f1, _ = make_pair(vols, inits, **kw)
+    f1.step(6)
+    blob = f1.state()
+    f1.step(6)
+    a = f1.params_host()
+    f2, _ = make_pair(vols, inits, **kw)
+    f2.step(12)
+    b = f2.params_host()
+    assert np.array_equal(a, b)
+    f3, _ = make_pair(vols, inits, **kw)
+    f3.load_state(blob)
+    f3.step(6)
+    c = f3.params_host()
+    assert np.array_equal(a, c)
+    assert np.array_equal(f1.groups(), f3.groups())
+    for f in (f1, f2, f3):
+        f.close()
+
+
+def test_nonfinite_signal_is_rejected():
+    import paper_2604_00250_gb300 as prism
+    vol = P.random_volume((3, 3, 3), seed=2)
+    sig = vol.signal.copy()
+    sig[4, 7] = np.nan
+    from tests.helpers import gpu_volume
+    v = gpu_volume(vol)
+    v.signal = sig
+    with pytest.raises(prism.PrismError) as e:
+        prism.Fitter([v], prism.options(K=2))
+    assert e.value.code == 5
