@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Benchmark of the PRISM fit on one GB300 (or N, one process per GPU).
+
+Workload: the HCP-shaped whole brain -- 145 x 174 x 145 grid, ellipsoid mask of
+740,110 voxels, 288 measurements (18 b=0 + 90 at each of b = 1000/2000/3000),
+SNR 30 Rician, K = 3, MSE, repulsion + sparsity + neighbour coherence (Huber-
+Laplacian and directional continuity) inside mask-cropped 16^3 patches. One step
+= one iteration of the fit over the whole volume: synthesis, calibration-free
+MSE, hand-written adjoint, priors and the Adam update of every parameter, in the
+fused persistent kernel replayed from a CUDA graph.
+
+Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle on a
+bounded sample of the same workload instead.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "voxel-iterations/s fused fwd+adjoint+Adam vs unfused, same GB300; % of roofline"
+UNIT = "voxel-iterations/s"
+WORKLOAD = "hcp_shaped_brain_145x174x145_ellipsoid_mask_N288_K3_mse_patch16"
+K_FIB = 3
+PRIORS = dict(lam_rep=0.01, lam_sparse=0.02, lam_sp=0.01, lam_dir=0.005)
+
+# FP32 operations per (voxel, measurement) pair of the fused kernel's hot loop, K = 3,
+# MSE, no calibration (fused multiply-add = 2): 20 + 31 K.
+FLOPS_PER_PAIR = 20 + 31 * K_FIB
+# FP32 peak: 152 SMs x 128 lanes x 2 flops x 2070 MHz (maximum SM clock).
+PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cfg_dict(V, extra=None):
+    d = {"workload": WORKLOAD, "voxels": int(V), "n_meas": 288, "K": K_FIB, "loss": "mse", "patch_dim": 16,
+         "priors": "repulsion+sparsity+huber_laplacian+directional_continuity",
+         "l2": "inputs larger than L2: 854 MB packed signal read every step"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while active."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 9:
+                rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no sample"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def make_brain(seed, device, scale=1.0):
+    import phantoms as P
+    if scale == 1.0:
+        return P.brain_phantom(seed=seed, device=device)
+    shape = tuple(int(round(s * scale)) for s in (145, 174, 145))
+    semi = tuple(a * scale for a in (52.8, 63.4, 52.8))
+    return P.brain_phantom(seed=seed, device=device, shape=shape, semi=semi)
+
+
+def patch_sample(vol, n_patches, patch_dim=16):
+    """Ids of the n fullest 16^3 patches (a bounded, deterministic sample of the volume)."""
+    mask = vol.mask.astype(bool)
+    coords = np.argwhere(mask)
+    pshape = tuple(-(-s // patch_dim) for s in mask.shape)
+    pid = np.ravel_multi_index(tuple((coords // patch_dim).T), pshape)
+    ids, counts = np.unique(pid, return_counts=True)
+    order = np.argsort(-counts, kind="stable")
+    return ids[order[:n_patches]], int(counts[order[:n_patches]].sum())
+
+
+def oracle_rate(vol, n_patches, iters, warm=1):
+    """Oracle voxel-iterations/s on whole patches of the workload (host cores)."""
+    import torch
+    import phantoms as P
+    from oracle import prism_oracle as O
+    ids, nvox = patch_sample(vol, n_patches)
+    o = O.Options(K=K_FIB, loss="mse", patch_dim=16, **PRIORS)
+    ov = O.OracleVolume(vol.mask, vol.signal, vol.bvals, vol.bvecs, o, patches=ids)
+    th = torch.as_tensor(P.default_init(ov.n_vox, K_FIB, 0)).double()
+    gp = O.group_init(ov)
+    adam = O.Adam(o)
+    times = []
+    for it in range(warm + iters):
+        t0 = time.perf_counter()
+        adam.t += 1
+        J, _, g, _ = O.value_and_grad(ov, th, gp, n_norm=ov.n_mask)
+        th = adam.step("theta", th, g)
+        times.append(time.perf_counter() - t0)
+    dt = sum(times[warm:])
+    return nvox * iters / dt, nvox, dt, torch.get_num_threads()
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import torch
+    vol = make_brain(args.seed, "cpu", args.brain_scale)
+    V = vol.n_vox
+    ids, nvox = patch_sample(vol, 1)
+    import phantoms as P
+    from oracle import prism_oracle as O
+    o = O.Options(K=K_FIB, loss="mse", patch_dim=16, **PRIORS)
+    ov = O.OracleVolume(vol.mask, vol.signal, vol.bvals, vol.bvecs, o, patches=ids)
+    th = torch.as_tensor(P.default_init(ov.n_vox, K_FIB, 0)).double()
+    gp = O.group_init(ov)
+    adam = O.Adam(o)
+
+    def one():
+        adam.t += 1
+        _, _, g, _ = O.value_and_grad(ov, th, gp, n_norm=ov.n_mask)
+        return adam.step("theta", th, g)
+
+    for _ in range(args.warmup):
+        th = one()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        th = one()
+    dt = time.perf_counter() - t0
+    value = nvox * args.steps / dt
+    cores = torch.get_num_threads()
+    sample = f"one 16^3 patch ({nvox} voxels) of the {V}-voxel brain per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg_dict(V, {"sample": sample}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    import types
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    import paper_2604_00250_gb300 as prism
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    vol = make_brain(args.seed + rank, "cuda", args.brain_scale)
+    V = vol.n_vox
+    N = vol.n_meas
+    sig_dev = torch.as_tensor(vol.signal, device=dev)
+    vdev = types.SimpleNamespace(mask=vol.mask, signal=sig_dev, bvals=vol.bvals, bvecs=vol.bvecs, init=None)
+    opts = prism.options(K=K_FIB, loss="mse", patch_dim=16, fused=1, use_graph=1, autotune=int(args.autotune),
+                         **PRIORS)
+    f = prism.Fitter([vdev], opts)
+    stream = torch.cuda.current_stream()
+    # ---- timed region: K fused iterations (graph replay), inputs resident in HBM
+    f.step(args.warmup)
+    f.sync()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.25)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    f.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    barrier()
+    ck = clocks.stop()
+    f.sync()
+    ms_total = max_over_ranks(e0.elapsed_time(e1))
+    ms_step = ms_total / args.steps
+    value = world * V * args.steps / (ms_total / 1e3)
+    # ---- live per-kernel timing (CUDA events around each kernel class, no graph)
+    prof = f.profile(min(args.steps, 50))
+    fused_ms = prof["fused_ms"]
+    achieved = V * N * FLOPS_PER_PAIR / (fused_ms / 1e3) / 1e12
+    loss_last = float(f.loss()[0])
+    tile = {"threads_per_voxel": None}
+    f.close()
+    # ---- plain path: separate launches per patch and step, no graph
+    unfused = None
+    if not args.no_unfused:
+        fu = prism.Fitter([vdev], prism.options(K=K_FIB, loss="mse", patch_dim=16, fused=0, use_graph=0, **PRIORS))
+        fu.step(2)
+        fu.sync()
+        n_u = 5
+        u0 = torch.cuda.Event(enable_timing=True)
+        u1 = torch.cuda.Event(enable_timing=True)
+        u0.record(stream)
+        fu.step(n_u)
+        u1.record(stream)
+        u1.synchronize()
+        fu.sync()
+        ms_u = max_over_ranks(u0.elapsed_time(u1)) / n_u
+        unfused = {"value": world * V / (ms_u / 1e3), "ms_per_step": ms_u, "steps": n_u,
+                   "launches_per_step": None}
+        fu.close()
+    # ---- end to end through prism_fit with HOST buffers (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        sig_host = torch.empty(vol.signal.shape, dtype=torch.float32, pin_memory=True)
+        sig_host.copy_(torch.as_tensor(vol.signal))
+        vhost = types.SimpleNamespace(mask=vol.mask, signal=sig_host, bvals=vol.bvals, bvecs=vol.bvecs, init=None)
+        n_e2e = args.e2e_iters
+        out = torch.empty((V, 4 * K_FIB + 5), dtype=torch.float32, pin_memory=True)
+        import ctypes
+        from paper_2604_00250_gb300 import _lib
+        lib = _lib.load()
+        keep = []
+        arr, nv = prism._volumes_array([vhost], keep)
+        loss_out = np.empty(1, dtype=np.float64)
+        barrier()
+        t0 = time.perf_counter()
+        _lib.check(lib.prism_fit(arr, nv, ctypes.byref(opts), n_e2e, ctypes.c_void_p(out.data_ptr()),
+                                 loss_out.ctypes.data, prism.MEM_HOST, ctypes.c_void_p(stream.cuda_stream)))
+        torch.cuda.synchronize()
+        dt = max_over_ranks(time.perf_counter() - t0)
+        h2d = sig_host.numel() * 4 + vol.mask.size + N * 16
+        d2h = out.numel() * 4 + 8
+        e2e = {"value": world * V * n_e2e / dt, "unit": UNIT, "h2d_bytes_per_step": h2d / n_e2e,
+               "d2h_bytes_per_step": d2h / n_e2e, "iterations": n_e2e, "seconds": dt,
+               "call": "prism_fit (init + iterations + readout), pinned host signal and parameters"}
+    # ---- CPU baseline: the FP64 oracle on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, nvox, dt, cores = oracle_rate(vol, args.cpu_patches, args.cpu_iters)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{args.cpu_patches} fullest 16^3 patches ({nvox} voxels) x {args.cpu_iters} iterations, "
+                         f"{dt:.1f} s"}
+    launches = (2 if PRIORS["lam_sp"] > 0 else 1) + 2
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": cfg_dict(V, {"timing": "CUDA events, graph replay, max over ranks",
+                                       "brain_scale": args.brain_scale}),
+                "roofline": {"bound": "alu", "achieved": achieved, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
+                             "frac": achieved / PEAK_FP32_TFLOPS, "traffic": None,
+                             "kernel": "k_iter_fused", "kernel_ms": fused_ms,
+                             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
+                "unfused": unfused,
+                "speedup_vs_unfused": (value / unfused["value"]) if unfused else None,
+                "profile_ms": prof, "final_loss": loss_last,
+                "clocks": ck, "e2e": e2e, "cpu_baseline": cpu,
+                "gpu_launches": launches * args.steps}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--brain-scale", type=float, default=1.0,
+                    help="scale the brain grid (profiling of smaller cases; 1.0 = the benchmark workload)")
+    ap.add_argument("--e2e-iters", type=int, default=500)
+    ap.add_argument("--cpu-patches", type=int, default=4)
+    ap.add_argument("--cpu-iters", type=int, default=20)
+    ap.add_argument("--no-unfused", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

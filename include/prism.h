@@ -164,6 +164,16 @@ int prism_forward(prism_handle* h, const float* theta, const float* groups, floa
  */
 int prism_backward(prism_handle* h, float* grad_theta, float* grad_groups, void* stream);
 
+/*
+ * Timing probe: enqueues n_iters >= 1 fused iterations WITHOUT the CUDA graph, with CUDA
+ * events on `stream` around each kernel class, waits for them, and writes the average
+ * milliseconds per iteration to ms_out (HOST float[4]): [0] the fused iteration kernel,
+ * [1] the neighbour-prior preparation kernel, [2] the group kernels (bias gradient,
+ * reductions, group Adam), [3] the whole iteration. The iterations are real updates.
+ * E_STATE on a handle created with fused = 0.
+ */
+int prism_profile(prism_handle* h, int32_t n_iters, void* stream, float* ms_out);
+
 /* Checkpoint: parameters, Adam moments, step counter and group state as one blob. */
 int prism_state_size(const prism_handle* h, int64_t* bytes);
 int prism_get_state(prism_handle* h, void* host_buf, int64_t bytes, void* stream);

@@ -124,7 +124,7 @@ class OracleVolume:
         self.sel = sel
         self.coords = coords_all[sel]
         self.pid = pid_all[sel]
-        sig = np.asarray(signal, dtype=np.float64)[sel]
+        sig = np.asarray(signal)[sel].astype(np.float64)
         self.bvals = torch.as_tensor(np.asarray(bvals, dtype=np.float64))
         self.bvecs = torch.as_tensor(np.asarray(bvecs, dtype=np.float64))
         b0 = self.bvals.numpy() <= B0_MAX
@@ -137,9 +137,9 @@ class OracleVolume:
         # R18: pooled std of normalised b0 repeats (computed on the full volume).
         nb0 = int(b0.sum())
         if nb0 >= 2:
-            full = np.asarray(signal, dtype=np.float64)
-            fb0 = full[:, b0] / full[:, b0].mean(axis=1, keepdims=True)
-            var = np.sum((fb0 - 1.0) ** 2) / (full.shape[0] * (nb0 - 1))
+            full_b0 = np.asarray(signal)[:, b0].astype(np.float64)
+            fb0 = full_b0 / full_b0.mean(axis=1, keepdims=True)
+            var = np.sum((fb0 - 1.0) ** 2) / (full_b0.shape[0] * (nb0 - 1))
             self.sigma0 = max(math.sqrt(var), 1e-3)
         else:
             self.sigma0 = opts.sigma_init

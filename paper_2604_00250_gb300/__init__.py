@@ -253,6 +253,12 @@ class Fitter:
                                             ctypes.c_void_p(gg.data_ptr()), _stream_ptr(stream)))
         return gth, gg
 
+    def profile(self, n_iters=10, stream=None):
+        """Average ms per iteration: fused kernel, prior preparation, group kernels, total."""
+        ms = (ctypes.c_float * 4)()
+        _lib.check(self._lib.prism_profile(self._h, int(n_iters), _stream_ptr(stream), ms))
+        return dict(fused_ms=ms[0], prep_ms=ms[1], group_ms=ms[2], iter_ms=ms[3])
+
     # -- checkpoint ------------------------------------------------------------------
     def state(self):
         n = ctypes.c_int64()

@@ -950,6 +950,49 @@ extern "C" int prism_backward(prism_handle* h, float* grad_theta, float* grad_gr
   return PRISM_OK;
 }
 
+extern "C" int prism_profile(prism_handle* h, int32_t n_iters, void* stream, float* ms_out) {
+  if (!h || !ms_out || n_iters < 1) return fail(PRISM_E_INVALID_ARG, "NULL argument or n_iters < 1");
+  if (!h->opt.fused) return fail(PRISM_E_STATE, "prism_profile times the fused path; the handle is plain");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const IterArgs& a = h->ia;
+  cudaEvent_t ev[4];
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  double acc[4] = {0, 0, 0, 0};
+  int rc = PRISM_OK;
+  for (int i = 0; i < n_iters && rc == PRISM_OK; ++i) {
+    cudaError_t e = cudaEventRecord(ev[0], st);
+    if (e == cudaSuccess && h->opt.lam_sp > 0.f) e = h->ks->prior_prep(a, 0, h->ntiles, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
+    if (e == cudaSuccess)
+      e = h->ks->fused(a, h->opt.loss, h->cal ? 1 : 0, h->TPV, h->fused_grid, h->NT, h->fused_smem, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2], st);
+    if (e == cudaSuccess && h->cal) e = launch_bias_grad(a, h->ga, st);
+    if (e == cudaSuccess) e = launch_group_reduce(a, h->ga, 1 | (h->cal ? 2 : 0), st);
+    if (e == cudaSuccess) e = launch_group_adam(a, h->ga, 1 | 2, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[3], st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "prism_profile");
+      break;
+    }
+    float t01 = 0, t12 = 0, t23 = 0, t03 = 0;
+    cudaEventElapsedTime(&t01, ev[0], ev[1]);
+    cudaEventElapsedTime(&t12, ev[1], ev[2]);
+    cudaEventElapsedTime(&t23, ev[2], ev[3]);
+    cudaEventElapsedTime(&t03, ev[0], ev[3]);
+    acc[0] += t12;
+    acc[1] += t01;
+    acc[2] += t23;
+    acc[3] += t03;
+    h->iters += 1;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (rc != PRISM_OK) return rc;
+  for (int k = 0; k < 4; ++k) ms_out[k] = static_cast<float>(acc[k] / n_iters);
+  h->forward_done = false;
+  return PRISM_OK;
+}
+
 namespace {
 struct StateHeader {
   uint32_t magic, version;
