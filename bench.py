@@ -33,9 +33,10 @@ WORKLOAD = "hcp_shaped_brain_145x174x145_ellipsoid_mask_N288_K3_mse_patch16"
 K_FIB = 3
 PRIORS = dict(lam_rep=0.01, lam_sparse=0.02, lam_sp=0.01, lam_dir=0.005)
 
-# FP32 operations per (voxel, measurement) pair of the fused kernel's hot loop, K = 3,
-# MSE, no calibration (fused multiply-add = 2): 20 + 31 K.
-FLOPS_PER_PAIR = 20 + 31 * K_FIB
+# FP32 floating-point operations per (voxel, measurement) pair of the fused kernel's hot
+# loop, MSE, no calibration, fused multiply-add = 2: 19 per measurement + 28 per fiber
+# (see the design doc for the itemised count).
+FLOPS_PER_PAIR = 19 + 28 * K_FIB
 # FP32 peak: 152 SMs x 128 lanes x 2 flops x 2070 MHz (maximum SM clock).
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 

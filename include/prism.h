@@ -90,7 +90,7 @@ typedef struct prism_options {
   int32_t fused;          /* 1: persistent fused iteration kernel; 0: plain unfused per-patch launches */
   int32_t use_graph;      /* 1: replay the fused iteration from a CUDA graph */
   int32_t threads_per_voxel; /* 1, 4 or 16 (measurements split across lanes); 0 = automatic */
-  int32_t cta_threads;    /* 128 or 256; 0 = automatic */
+  int32_t cta_threads;    /* plain path: 128 or 256 threads per CTA; 0 = automatic (the fused kernel uses 128) */
   int32_t autotune;       /* 1: time the candidate tile shapes at init and keep the fastest */
   int32_t seed;           /* seed of the default initialisation (init == NULL) */
   int32_t reserved[4];

@@ -663,6 +663,7 @@ int init_impl(prism_handle* h, const prism_volume* vols, int n_vols, cudaStream_
   // launch geometry of the fused kernel
   const int NW = h->NT / 32;
   h->fused_smem = static_cast<size_t>(h->Nmax) * sizeof(MeasRow) +
+                  static_cast<size_t>(kStages) * kChunk * h->TV * sizeof(float) +
                   (h->cal ? kNGrid * sizeof(float) + static_cast<size_t>(NW) * 2 * h->Nmax * sizeof(float) : 0);
   h->adj_smem = h->cal ? static_cast<size_t>(NW) * 2 * h->Nmax * sizeof(float) : 0;
   if (o.fused) {
@@ -679,7 +680,8 @@ int init_impl(prism_handle* h, const prism_volume* vols, int n_vols, cudaStream_
 
 int choose_shape(const prism_options& o, int64_t V, int* tpv, int* nt) {
   *tpv = o.threads_per_voxel ? o.threads_per_voxel : (V >= 32768 ? 1 : (V >= 4096 ? 4 : 16));
-  *nt = o.cta_threads ? o.cta_threads : 128;
+  // the fused kernel is compiled for 128-thread CTAs (4 resident per SM)
+  *nt = o.fused ? 128 : (o.cta_threads ? o.cta_threads : 128);
   return PRISM_OK;
 }
 
@@ -731,7 +733,7 @@ extern "C" int prism_fit_init(const prism_volume* vols, int32_t n_vols, const pr
   choose_shape(o, V, &tpv, &nt);
   if (o.autotune && o.fused) {
     // Time each candidate tile shape for a few iterations on the real data; keep the fastest.
-    const int cands[6][2] = {{1, 128}, {1, 256}, {4, 128}, {4, 256}, {16, 128}, {16, 256}};
+    const int cands[3][2] = {{1, 128}, {4, 128}, {16, 128}};
     float best = 1e30f;
     prism_options oc = o;
     oc.use_graph = 0;
@@ -741,7 +743,6 @@ extern "C" int prism_fit_init(const prism_volume* vols, int32_t n_vols, const pr
     CK(cudaEventCreate(&e1));
     for (const auto& c : cands) {
       if (o.threads_per_voxel && c[0] != o.threads_per_voxel) continue;
-      if (o.cta_threads && c[1] != o.cta_threads) continue;
       prism_handle* hc = nullptr;
       if (create_handle(vols, n_vols, oc, c[0], c[1], st, &hc) != PRISM_OK) {
         g_err.clear();

@@ -23,11 +23,16 @@ constexpr float kNormEps2 = 1e-24f;                  // |v| clamp 1e-12, squared
 // Device status word bits (read by prism_sync).
 enum : int { kStTimeout = 1, kStNonfinite = 2 };
 
-// One row of the per-measurement table (48 bytes, 16-byte aligned for the bulk copy).
+// One row of the per-measurement table (64 bytes, 16-byte aligned for the bulk copy).
+// With c = d_k . g_n and x = c^2 the fiber terms of Eq. 4 are
+//   e1 = exp(-b D_par x) = 2^(nkpar x),
+//   p  = exp(-b (D_par x + D_perp (1 - x))) = 2^(nkperp + nkd x),
+//   E_wm = f_in e1 + (1 - f_in) p,   dE_wm/dc = c (An f_in e1 + Bn (1 - f_in) p).
 struct __align__(16) MeasRow {
-  float gx, gy, gz, kpar;     // g_n; b_n D_par log2(e)
-  float kperp, ecsf, egm, eres;  // b_n D_perp log2(e); E_csf, E_gm, E_res at b_n (Eq. 3)
-  float A, beta, dpar2, dperp2;  // exp(alpha_n), beta_n (Eq. 5); 2 b_n D_par, 2 b_n D_perp
+  float gx, gy, gz, nkpar;       // g_n; -b D_par log2(e)
+  float nkperp, nkd, ecsf, egm;  // -b D_perp log2(e); -b (D_par - D_perp) log2(e); E_csf, E_gm (Eq. 3)
+  float eres, An, Bn, A;         // E_res; -2 b D_par; 2 b (D_perp - D_par); exp(alpha_n) (Eq. 5)
+  float beta, pad0, pad1, pad2;  // beta_n
 };
 
 // A tile: up to TV voxels of one patch, processed by one CTA.
@@ -134,6 +139,10 @@ __device__ __forceinline__ void tma_bulk_g2s(void* dst, const void* src, uint32_
           smem_u32(dst)),
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
+}
+// Bulk prefetch of [p, p + bytes) into L2 (16-byte aligned address, size a multiple of 16).
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 // Bounded wait on phase `parity`; false if it did not complete within the limit.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {

@@ -204,11 +204,13 @@ __device__ __forceinline__ float tv_term(const float* blr, int x, int y, int z, 
   return val;
 }
 
-// Voxel-level gradient accumulators of the data term (unscaled), per thread.
+// Voxel-level gradient accumulators of the data term (unscaled), per thread:
+// q = dJ/dS at each measurement; gwa_k = sum q e1_k, gwb_k = sum q p_k (so that
+// dJ/df_wm,k and dJ/df_in follow after the loop), gd_k = sum q dE_k/dc g.
 template <int K>
 struct Acc {
-  float gS0, gcsf, ggm, gres, gin;
-  float gw[K];
+  float gS0, gcsf, ggm, gres;
+  float gwa[K], gwb[K];
   float gd[K][3];
   float l1, l2, l3;   // MSE: sum r^2 | NLL: sum (y-|yh|)^2, sum |y yh| Q, sum L
   float u;            // sum_n r A B S (= dJ/dU unscaled, calibration)
@@ -216,10 +218,10 @@ struct Acc {
 
 template <int K>
 __device__ __forceinline__ void acc_zero(Acc<K>& A) {
-  A.gS0 = A.gcsf = A.ggm = A.gres = A.gin = 0.f;
+  A.gS0 = A.gcsf = A.ggm = A.gres = 0.f;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    A.gw[k] = 0.f;
+    A.gwa[k] = A.gwb[k] = 0.f;
     A.gd[k][0] = A.gd[k][1] = A.gd[k][2] = 0.f;
   }
   A.l1 = A.l2 = A.l3 = A.u = 0.f;
@@ -232,10 +234,10 @@ __device__ __forceinline__ void acc_reduce_tpv(Acc<K>& A) {
     A.gcsf = warp_sum_range<1, TPV / 2>(A.gcsf);
     A.ggm = warp_sum_range<1, TPV / 2>(A.ggm);
     A.gres = warp_sum_range<1, TPV / 2>(A.gres);
-    A.gin = warp_sum_range<1, TPV / 2>(A.gin);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      A.gw[k] = warp_sum_range<1, TPV / 2>(A.gw[k]);
+      A.gwa[k] = warp_sum_range<1, TPV / 2>(A.gwa[k]);
+      A.gwb[k] = warp_sum_range<1, TPV / 2>(A.gwb[k]);
 #pragma unroll
       for (int c = 0; c < 3; ++c) A.gd[k][c] = warp_sum_range<1, TPV / 2>(A.gd[k][c]);
     }
@@ -247,24 +249,24 @@ __device__ __forceinline__ void acc_reduce_tpv(Acc<K>& A) {
 }
 
 // One (voxel, measurement) pair: forward model (Eqs. 2-5), data-term derivative, and
-// accumulation of the adjoint. `rr_ext` (>= -inf) replaces the residual derivative when
-// the caller supplies dL/dy_hat (plain adjoint); returns the unscaled u = r A B S.
+// accumulation of the adjoint. With EXT_R the caller supplies dL/dy_hat (plain
+// adjoint); rr_out returns dL/dy_hat (unscaled) and u_out the unscaled r A B S.
+// `ffin` / `fomf` are f_wm,k f_in and f_wm,k (1 - f_in).
 template <int K, int LOSS, bool CAL, bool EXT_R>
-__device__ __forceinline__ void pair(const Vox<K>& P, const MeasRow& R, float yv, float B, float inv_s2,
-                                     float r_ext, Acc<K>& A, float& rr_out, float& u_out) {
+__device__ __forceinline__ void pair(const Vox<K>& P, const float (&ffin)[K], const float (&fomf)[K],
+                                     const MeasRow& R, float yv, float B, float inv_s2, float r_ext, Acc<K>& A,
+                                     float& rr_out, float& u_out) {
   float T = P.f[0] * R.ecsf;
   T = fmaf(P.f[1], R.egm, T);
   T = fmaf(P.f[K + 2], R.eres, T);
-  float E[K], e1[K], p[K], c[K];
+  float e1[K], p[K], c[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     c[k] = fmaf(P.d[k][0], R.gx, fmaf(P.d[k][1], R.gy, P.d[k][2] * R.gz));
     const float c2 = c[k] * c[k];
-    e1[k] = ex2f_(-R.kpar * c2);
-    const float e2 = ex2f_(fmaf(R.kperp, c2, -R.kperp));
-    p[k] = e1[k] * e2;
-    E[k] = fmaf(P.fin, e1[k], P.omf * p[k]);
-    T = fmaf(P.f[2 + k], E[k], T);
+    e1[k] = ex2f_(R.nkpar * c2);
+    p[k] = ex2f_(fmaf(R.nkd, c2, R.nkperp));
+    T = fmaf(ffin[k], e1[k], fmaf(fomf[k], p[k], T));
   }
   const float S = P.S0 * T;
   float yh, AB = 1.f;
@@ -301,19 +303,25 @@ __device__ __forceinline__ void pair(const Vox<K>& P, const MeasRow& R, float yv
   A.gcsf = fmaf(q, R.ecsf, A.gcsf);
   A.ggm = fmaf(q, R.egm, A.ggm);
   A.gres = fmaf(q, R.eres, A.gres);
-  const float cperp = R.dperp2 * P.omf;
-  float gin = 0.f;
+  const float anf = R.An * P.fin, bno = R.Bn * P.omf;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    A.gw[k] = fmaf(q, E[k], A.gw[k]);
-    gin = fmaf(P.f[2 + k], e1[k] - p[k], gin);
-    const float dE = c[k] * fmaf(-R.dpar2, E[k], cperp * p[k]);   // dE_wm/dc
-    const float w = q * dE;
+    A.gwa[k] = fmaf(q, e1[k], A.gwa[k]);
+    A.gwb[k] = fmaf(q, p[k], A.gwb[k]);
+    const float w = (q * c[k]) * fmaf(bno, p[k], anf * e1[k]);   // q dE_wm/dc
     A.gd[k][0] = fmaf(w, R.gx, A.gd[k][0]);
     A.gd[k][1] = fmaf(w, R.gy, A.gd[k][1]);
     A.gd[k][2] = fmaf(w, R.gz, A.gd[k][2]);
   }
-  A.gin = fmaf(q, gin, A.gin);
+}
+
+template <int K>
+__device__ __forceinline__ void fiber_weights(const Vox<K>& P, float (&ffin)[K], float (&fomf)[K]) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    ffin[k] = P.f[2 + k] * P.fin;
+    fomf[k] = P.f[2 + k] * P.omf;
+  }
 }
 
 // Scaled data-term gradient w.r.t. transformed parameters.
@@ -325,14 +333,16 @@ __device__ __forceinline__ void data_grad(const Vox<K>& P, const Acc<K>& A, floa
   gf[0] = A.gcsf * sS;
   gf[1] = A.ggm * sS;
   gf[K + 2] = A.gres * sS;
+  float gin = 0.f;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    gf[2 + k] = A.gw[k] * sS;
+    gf[2 + k] = fmaf(P.fin, A.gwa[k], P.omf * A.gwb[k]) * sS;   // sum q E_wm,k
+    gin = fmaf(P.f[2 + k], A.gwa[k] - A.gwb[k], gin);          // sum q sum_k f_k (e1 - p)
     const float w = sS * P.f[2 + k];
 #pragma unroll
     for (int c = 0; c < 3; ++c) gd[k][c] = A.gd[k][c] * w;
   }
-  gfin = A.gin * sS;
+  gfin = gin * sS;
 }
 
 __device__ __forceinline__ void block_reduce3(double v0, double v1, double v2, double (*s_red)[3],
@@ -363,43 +373,87 @@ __device__ __forceinline__ void block_reduce3(double v0, double v1, double v2, d
 // ===========================================================================
 // Fused iteration: one persistent kernel over the tile queue does synthesis,
 // calibration, data term, adjoint, priors, chain rule and the voxel Adam update.
+//
+// The tile's packed signal block ([N][TV] floats, contiguous) streams through a
+// ring of kStages shared-memory buffers of kChunk measurements each, filled by bulk
+// TMA copies (cp.async.bulk) issued by thread 0 and tracked by full / empty
+// mbarriers, so the hot loop reads y from shared memory. The measurement table and
+// the bias grid arrive the same way whenever the group changes.
 // ===========================================================================
+constexpr int kChunk = 16;    // measurements per ring stage
+constexpr int kStages = 4;    // ring depth
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 template <int K, int TPV, int LOSS, bool CAL>
-__global__ void __launch_bounds__(256) k_iter_fused(const IterArgs a) {
+__global__ void __launch_bounds__(128, 4) k_iter_fused(const IterArgs a) {
   constexpr int NF = K + 3, Q = 4 * K + 5, XF = 4 * K + 3;
+  static_assert(kChunk % TPV == 0, "chunk must split evenly across the voxel's lanes");
   extern __shared__ __align__(16) unsigned char smem[];
+  const int TV = a.TV, Vp = a.Vpad;
   MeasRow* s_tab = reinterpret_cast<MeasRow*>(smem);
-  float* s_blr = reinterpret_cast<float*>(s_tab + a.Nmax);
-  float* s_ab = s_blr + (CAL ? kNGrid : 0);
-  __shared__ uint64_t s_bar;
+  float* s_ring = reinterpret_cast<float*>(s_tab + a.Nmax);           // [kStages][kChunk][TV]
+  float* s_blr = s_ring + kStages * kChunk * TV;                        // [512] (calibration)
+  float* s_ab = s_blr + (CAL ? kNGrid : 0);                             // [NW][2][Nmax] (calibration)
+  __shared__ uint64_t s_bar;                 // table / bias grid
+  __shared__ uint64_t s_full[kStages];
+  __shared__ uint64_t s_empty[kStages];
   __shared__ int s_tile;
   __shared__ double s_red[8][3];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int NW = blockDim.x >> 5;
   const int vl = tid / TPV, js = tid % TPV;
-  const int TV = a.TV, Vp = a.Vpad;
   const int step = *a.step;
   const int par = step & 1;
   const float* xf_cur = a.xf + static_cast<size_t>(par) * XF * Vp;
   float* xf_nxt = a.xf + static_cast<size_t>(par ^ 1) * XF * Vp;
   if (tid == 0) {
     mbar_init(&s_bar, 1);
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&s_full[s], 1);
+      mbar_init(&s_empty[s], NW);
+    }
     fence_mbar_init();
   }
   __syncthreads();
   const float stepsz = a.adamc[0], isbc2 = a.adamc[1];
   int cur_group = -1;
-  uint32_t phase = 0;
+  uint32_t tphase = 0;
+  uint32_t gchunk = 0;   // ring chunks consumed by this CTA so far
   bool failed = false;
+
+  // Thread 0: copy chunk j of the tile's signal block into ring slot of global chunk g.
+  auto issue = [&](uint32_t g, const float* ysrc, int j, int N) {
+    const int s = g % kStages;
+    const uint32_t use = g / kStages;
+    if (use >= 1 && !failed) {
+      if (!mbar_wait(&s_empty[s], (use - 1) & 1)) {
+        atomicOr(a.status, kStTimeout);
+        failed = true;
+      }
+    }
+    const int cnt = min(kChunk, N - j * kChunk);
+    const uint32_t bytes = static_cast<uint32_t>(cnt) * TV * 4u;
+    fence_proxy_async_smem();
+    mbar_expect_tx(&s_full[s], bytes);
+    tma_bulk_g2s(s_ring + static_cast<size_t>(s) * kChunk * TV, ysrc + static_cast<size_t>(j) * kChunk * TV,
+                 bytes, &s_full[s]);
+  };
 
   for (;;) {
     if (tid == 0) s_tile = atomicAdd(a.queue, 1);
     __syncthreads();
     const int t = s_tile;
     if (t >= a.ntiles) break;
+    if (__syncthreads_or(failed)) break;   // block-uniform exit after a timed-out wait
     const Tile tl = a.tiles[t];
     const GroupDev gr = a.groups[tl.group];
     const int N = tl.n_meas;
+    const int nch = (N + kChunk - 1) / kChunk;
+    const float* __restrict__ ysrc = a.y + tl.y_off;
     if (tl.group != cur_group) {
       if (tid == 0) {
         fence_proxy_async_smem();
@@ -408,22 +462,39 @@ __global__ void __launch_bounds__(256) k_iter_fused(const IterArgs a) {
         tma_bulk_g2s(s_tab, a.table + gr.table_off, tb, &s_bar);
         if (CAL) tma_bulk_g2s(s_blr, a.gparams + gr.gp_off + 4 + 2 * gr.N4, kNGrid * 4u, &s_bar);
       }
-      const bool ok_wait = mbar_wait(&s_bar, phase);
-      if (__syncthreads_or(!ok_wait)) {   // block-uniform decision
+      if (!mbar_wait(&s_bar, tphase)) {
         if (tid == 0) atomicOr(a.status, kStTimeout);
-        mbar_wait(&s_bar, phase);   // let an in-flight copy land before leaving
         failed = true;
-        break;
       }
-      phase ^= 1;
+      tphase ^= 1;
       cur_group = tl.group;
     }
+    // prologue: the first kStages - 1 chunks of this tile, and an L2 prefetch of the rows
+    // the epilogue reads (parameters, Adam moments, neighbour-prior data of the tile)
+    if (tid == 0) {
+      for (int j = 0; j < kStages - 1 && j < nch; ++j) issue(gchunk + j, ysrc, j, N);
+      const uint32_t rb = static_cast<uint32_t>(TV) * 4u;
+      for (int q = 0; q < Q; ++q) {
+        const size_t o = static_cast<size_t>(q) * Vp + tl.slot0;
+        prefetch_l2(a.theta + o, rb);
+        prefetch_l2(a.m + o, rb);
+        prefetch_l2(a.v + o, rb);
+      }
+      if (a.nb_priors) {
+        for (int e = 0; e < 6; ++e) prefetch_l2(a.nbr + static_cast<size_t>(e) * Vp + tl.slot0, rb);
+        if (a.lam_sp > 0.f)
+          for (int c = 0; c < NF; ++c) prefetch_l2(a.hsp + static_cast<size_t>(c) * Vp + tl.slot0, rb);
+      }
+    }
+
     const int slot = tl.slot0 + vl;
     const bool act = vl < tl.count;
-    float th[Q];
-    load_theta<K>(a.theta, Vp, slot, act, th);
     Vox<K> P;
-    transform<K>(th, P);
+    {
+      float th[Q];
+      load_theta<K>(a.theta, Vp, slot, act, th);
+      transform<K>(th, P);
+    }
     float inv_s2 = 0.f, slog = 0.f;
     if (LOSS == kLossNLL) {
       slog = a.gparams[gr.gp_off];
@@ -438,27 +509,41 @@ __global__ void __launch_bounds__(256) k_iter_fused(const IterArgs a) {
     }
     Acc<K> A;
     acc_zero<K>(A);
-    const float* __restrict__ yt = a.y + tl.y_off;
-    const int iters = (N + TPV - 1) / TPV;
-#pragma unroll 2
-    for (int i = 0; i < iters; ++i) {
-      const int n = i * TPV + js;
-      const bool ok = act && (n < N);
-      float rr = 0.f, u = 0.f;
-      if (ok) {
-        const MeasRow R = s_tab[n];
-        const float yv = __ldg(yt + static_cast<size_t>(n) * TV + vl);
-        pair<K, LOSS, CAL, false>(P, R, yv, B, inv_s2, 0.f, A, rr, u);
+    float ffin[K], fomf[K];
+    fiber_weights<K>(P, ffin, fomf);
+    for (int j = 0; j < nch; ++j) {
+      const uint32_t g = gchunk + j;
+      if (tid == 0 && j + kStages - 1 < nch) issue(g + kStages - 1, ysrc, j + kStages - 1, N);
+      const int s = g % kStages;
+      if (!failed && !mbar_wait(&s_full[s], (g / kStages) & 1)) {
+        atomicOr(a.status, kStTimeout);
+        failed = true;
       }
-      if (CAL) {
-        float su = warp_sum_range<TPV, 16>(ok ? u : 0.f);
-        float sr = warp_sum_range<TPV, 16>(ok ? rr : 0.f);
-        if (lane < TPV && n < N) {
-          s_ab[(warp * 2) * a.Nmax + n] = su;
-          s_ab[(warp * 2 + 1) * a.Nmax + n] = sr;
+      const float* __restrict__ yc = s_ring + static_cast<size_t>(s) * kChunk * TV;
+      const int nb = j * kChunk;
+      const int cnt = min(kChunk, N - nb);
+#pragma unroll 4
+      for (int i = 0; i < kChunk / TPV; ++i) {
+        const int nl = i * TPV + js;
+        const bool ok = act && (nl < cnt);
+        float rr = 0.f, u = 0.f;
+        if (ok) {
+          const MeasRow R = s_tab[nb + nl];
+          pair<K, LOSS, CAL, false>(P, ffin, fomf, R, yc[nl * TV + vl], B, inv_s2, 0.f, A, rr, u);
+        }
+        if (CAL) {
+          float su = warp_sum_range<TPV, 16>(ok ? u : 0.f);
+          float sr = warp_sum_range<TPV, 16>(ok ? rr : 0.f);
+          if (lane < TPV && nl < cnt) {
+            s_ab[(warp * 2) * a.Nmax + nb + nl] = su;
+            s_ab[(warp * 2 + 1) * a.Nmax + nb + nl] = sr;
+          }
         }
       }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&s_empty[s]);
     }
+    gchunk += nch;
     acc_reduce_tpv<K, TPV>(A);
 
     // ---- data-term gradient and value
@@ -478,7 +563,9 @@ __global__ void __launch_bounds__(256) k_iter_fused(const IterArgs a) {
       const uint32_t fl = act ? a.vflag[slot] : 0u;
       ploss += tv_term(s_blr, cx, cy, cz, gr, fl, B, a.w_tv * gr.inv_M, a.tv_eps, gUv);
     }
-    // ---- chain rule and Adam
+    // ---- chain rule and Adam (raw parameters re-read: they are not kept live across the loop)
+    float th[Q];
+    load_theta<K>(a.theta, Vp, slot, act, th);
     float g[Q];
     chain_raw<K>(P, gS0, gf, gd, gfin, g);
     const bool writer = act && (js == 0);
@@ -506,19 +593,20 @@ __global__ void __launch_bounds__(256) k_iter_fused(const IterArgs a) {
     block_reduce3(writer ? static_cast<double>(dloss) : 0.0, writer ? static_cast<double>(dsig) : 0.0,
                   writer ? static_cast<double>(ploss) : 0.0, s_red, a.tile_red + 4 * static_cast<size_t>(t));
     if (CAL) {
-      // s_ab complete after block_reduce3's barrier
-      const int NW = blockDim.x >> 5;
       for (int e = tid; e < 2 * N; e += blockDim.x) {
         const int w2 = (e < N) ? 0 : 1;
         const int n = e - w2 * N;
-        float s = 0.f;
-        for (int w = 0; w < NW; ++w) s += s_ab[(w * 2 + w2) * a.Nmax + n];
-        a.tile_ab[tl.ab_off + e] = s * scale;
+        float sum = 0.f;
+        for (int w = 0; w < NW; ++w) sum += s_ab[(w * 2 + w2) * a.Nmax + n];
+        a.tile_ab[tl.ab_off + e] = sum * scale;
       }
     }
     __syncthreads();
   }
-  (void)failed;
+  if (failed && tid == 0) {
+    // let any copy still in flight land before the CTA's shared memory is released
+    for (int s = 0; s < kStages; ++s) mbar_wait(&s_full[s], 0), mbar_wait(&s_full[s], 1);
+  }
   // The last CTA to leave resets the queue for the next iteration.
   if (tid == 0) {
     __threadfence();
@@ -579,9 +667,9 @@ __global__ void __launch_bounds__(256) k_synth(const IterArgs a, const PlainArgs
     for (int k = 0; k < K; ++k) {
       const float c = fmaf(P.d[k][0], R.gx, fmaf(P.d[k][1], R.gy, P.d[k][2] * R.gz));
       const float c2 = c * c;
-      const float e1 = ex2f_(-R.kpar * c2);
-      const float e2 = ex2f_(fmaf(R.kperp, c2, -R.kperp));
-      T = fmaf(P.f[2 + k], fmaf(P.fin, e1, P.omf * e1 * e2), T);
+      const float e1 = ex2f_(R.nkpar * c2);
+      const float p = ex2f_(fmaf(R.nkd, c2, R.nkperp));
+      T = fmaf(P.f[2 + k], fmaf(P.fin, e1, P.omf * p), T);
     }
     const float S = P.S0 * T;
     pa.yhat[tl.y_off + static_cast<size_t>(n) * a.TV + vl] = CAL ? fmaf(R.A * B, S, R.beta) : S;
@@ -662,6 +750,8 @@ __global__ void __launch_bounds__(256) k_adjoint(const IterArgs a, const PlainAr
   }
   Acc<K> A;
   acc_zero<K>(A);
+  float ffin[K], fomf[K];
+  fiber_weights<K>(P, ffin, fomf);
   const int iters = (N + TPV - 1) / TPV;
   for (int i = 0; i < iters; ++i) {
     const int n = i * TPV + js;
@@ -669,7 +759,7 @@ __global__ void __launch_bounds__(256) k_adjoint(const IterArgs a, const PlainAr
     float rr = 0.f, u = 0.f;
     if (ok) {
       const size_t ix = tl.y_off + static_cast<size_t>(n) * a.TV + vl;
-      pair<K, kLossMSE, CAL, true>(P, tab[n], 0.f, B, 0.f, pa.r[ix], A, rr, u);
+      pair<K, kLossMSE, CAL, true>(P, ffin, fomf, tab[n], 0.f, B, 0.f, pa.r[ix], A, rr, u);
     }
     if (CAL) {
       float su = warp_sum_range<TPV, 16>(ok ? u : 0.f);
