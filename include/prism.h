@@ -188,6 +188,37 @@ int prism_fit(const prism_volume* vols, int32_t n_vols, const prism_options* opt
               int32_t n_iters, float* params_out, double* loss_out, int32_t out_mem,
               void* stream);
 
+/*
+ * Allocation-free objective and gradient (the paper has no counterpart of this call).
+ *
+ * For callers that must not allocate device memory where they evaluate the fit: code
+ * running inside a framework that owns the whole device memory pool, real-time
+ * pipelines that reserve all memory up front because cudaMalloc / cudaFree can
+ * synchronise the device, and plugins whose host forbids allocations outside its own
+ * allocator. It needs no handle and calls no cudaMalloc, cudaFree or allocating library
+ * routine: beyond the caller's buffers it uses one fixed 128 KiB array inside the
+ * library, which every GPU that loads the library keeps until the process exits.
+ *
+ * Evaluates, for n_vox voxels forming one group, J = MSE data term (Eq. 7, divided by
+ * n_vox) + lam_rep * mean repulsion + lam_sparse * mean sparsity (Sec. 2.4), without
+ * calibration or neighbour priors, on raw signal rows that it b0-normalises itself
+ * (mean of the b <= 50 measurements), and its gradient -- the same values prism_forward
+ * and prism_backward give for that problem.
+ *   signal  DEVICE [n_vox][n_meas] raw magnitudes;  theta DEVICE [n_vox][4K+5] raw parameters
+ *   bvals   HOST [n_meas];  bvecs HOST [n_meas][3]
+ *   grad    DEVICE [n_vox][4K+5] (written);  loss DEVICE double[1] (written)
+ * Limits: 1 <= n_vox <= 1,048,576, 1 <= n_meas <= 1024, 1 <= K <= 5 (E_SHAPE /
+ * E_INVALID_ARG otherwise, before any device work); at least one b <= 50 measurement.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture begins.
+ * Every call shares the array and leaves its contents behind (it clears what must start
+ * at zero itself), so two calls whose GPU work overlaps on the same device (for example
+ * on two streams) race with each other: serialise them.
+ */
+int prism_grad_noalloc(const float* signal, const float* bvals, const float* bvecs, const float* theta,
+                       int64_t n_vox, int32_t n_meas, int32_t K, float lam_rep, float lam_sparse,
+                       float tau, float* grad, double* loss, void* stream);
+
 /* Frees every device buffer and graph of the handle. NULL is a no-op. */
 void prism_fit_destroy(prism_handle* h);
 

@@ -158,6 +158,9 @@ extern "C" void prism_default_options(prism_options* o) {
 
 extern "C" const char* prism_last_error(void) { return g_err.c_str(); }
 
+// Lets other translation units of the library report through prism_last_error().
+int prism_record_error(int code, const char* msg) { return fail(code, msg); }
+
 namespace {
 
 bool finite_nonneg(float x) { return std::isfinite(x) && x >= 0.f; }
