@@ -34,9 +34,9 @@ K_FIB = 3
 PRIORS = dict(lam_rep=0.01, lam_sparse=0.02, lam_sp=0.01, lam_dir=0.005)
 
 # FP32 floating-point operations per (voxel, measurement) pair of the fused kernel's hot
-# loop, MSE, no calibration, fused multiply-add = 2: 19 per measurement + 28 per fiber
-# (see the design doc for the itemised count).
-FLOPS_PER_PAIR = 19 + 28 * K_FIB
+# loop on this workload (packed two-measurement path: MSE, no calibration), fused
+# multiply-add = 2: 17 per measurement + 28 per fiber (itemised in the design doc).
+FLOPS_PER_PAIR = 17 + 28 * K_FIB
 # FP32 peak: 152 SMs x 128 lanes x 2 flops x 2070 MHz (maximum SM clock).
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 

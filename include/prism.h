@@ -174,6 +174,15 @@ int prism_backward(prism_handle* h, float* grad_theta, float* grad_groups, void*
  */
 int prism_profile(prism_handle* h, int32_t n_iters, void* stream, float* ms_out);
 
+/*
+ * Pipe microbenchmark for roofline denominators: kind 0 = FP32 fused multiply-add,
+ * 1 = packed float2 FMA, 2 = special-function 2^x (ex2.approx), 3 = FP64 FMA. Runs a
+ * fixed amount of independent dependency chains on every SM of the current device and
+ * writes the achieved rate to *ops_per_s (flops, FMA = 2; for kind 2 exponentials/s).
+ * Synchronous; allocates a small sink buffer.
+ */
+int prism_microbench(int32_t kind, double* ops_per_s, void* stream);
+
 /* Checkpoint: parameters, Adam moments, step counter and group state as one blob. */
 int prism_state_size(const prism_handle* h, int64_t* bytes);
 int prism_get_state(prism_handle* h, void* host_buf, int64_t bytes, void* stream);

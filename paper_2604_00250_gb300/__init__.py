@@ -286,6 +286,14 @@ def fit(volumes, opts=None, n_iters=200, stream=None, **kw):
     return theta, loss
 
 
+def microbench(kind):
+    """Measured arithmetic rate of one pipe: "ffma", "ffma2" (flops/s), "ex2" (2^x per s), "dfma"."""
+    k = {"ffma": 0, "ffma2": 1, "ex2": 2, "dfma": 3}[kind]
+    r = ctypes.c_double()
+    _lib.check(_lib.load().prism_microbench(k, ctypes.byref(r), _stream_ptr(None)))
+    return r.value
+
+
 def _make_autograd():
     torch = _torch()
 

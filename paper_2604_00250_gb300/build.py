@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "libprism_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", INCLUDE, "-I", CSRC]
-SOURCES = ["prism_api.cu", "prism_aux.cu", "prism_noalloc.cu", "prism_k1.cu", "prism_k2.cu", "prism_k3.cu", "prism_k4.cu",
+SOURCES = ["prism_api.cu", "prism_aux.cu", "prism_noalloc.cu", "prism_ubench.cu", "prism_k1.cu", "prism_k2.cu", "prism_k3.cu", "prism_k4.cu",
            "prism_k5.cu"]
 HEADERS = ["prism_device.cuh", "prism_kernels.cuh", "prism_kset.cuh", "prism_launch.h", "bessel_fit.h"]
 

@@ -95,6 +95,8 @@ struct prism_handle {
   uint32_t *d_vcoord = nullptr, *d_vflag = nullptr;
   int64_t* d_row_off = nullptr;
   MeasRow* d_table = nullptr;
+  MeasPair* d_table2 = nullptr;
+  int64_t tab2_pairs = 0;
   double *d_tile_red = nullptr, *d_part2 = nullptr, *d_gred = nullptr, *d_gloss = nullptr;
   double *d_gprior = nullptr, *d_hist = nullptr;
   IterArgs ia{};
@@ -215,6 +217,7 @@ void fill_args(prism_handle* h) {
   a.Q = h->Q;
   a.Vpad = h->Vpad;
   a.TV = h->TV;
+  a.VW = 32 / h->TPV;
   a.ntiles = h->ntiles;
   a.Nmax = h->Nmax;
   a.G = h->G;
@@ -231,6 +234,7 @@ void fill_args(prism_handle* h) {
   a.vcoord = h->d_vcoord;
   a.vflag = h->d_vflag;
   a.table = h->d_table;
+  a.table2 = h->d_table2;
   a.gparams = h->d_gparams;
   a.gU = h->d_gU;
   a.tile_ab = h->d_tile_ab;
@@ -381,6 +385,8 @@ int build_plan(prism_handle* h, const prism_volume* vols, int n_vols, Plan& pl) 
     gr.calib = h->cal ? 1 : 0;
     gr.table_off = static_cast<int32_t>(tab);
     tab += v.n_meas;
+    gr.table2_off = static_cast<int32_t>(h->tab2_pairs);
+    h->tab2_pairs += ((v.n_meas + 3) & ~3) / 2;
     gr.gp_off = static_cast<int32_t>(gp);
     h->gp_layout[4 * g + 0] = gp;
     h->gp_layout[4 * g + 1] = gp + 4;
@@ -415,7 +421,7 @@ int build_plan(prism_handle* h, const prism_volume* vols, int n_vols, Plan& pl) 
             t.y_off = yoff;
             t.ab_off = static_cast<int32_t>(aboff);
             t.n_meas = v.n_meas;
-            yoff += static_cast<int64_t>(v.n_meas) * TV;
+            yoff += static_cast<int64_t>((v.n_meas + 3) & ~3) * TV;
             aboff += 2 * v.n_meas;
             for (int i = 0; i < t.count; ++i) {
               const int64_t gi = pv[s0 + i];
@@ -434,7 +440,7 @@ int build_plan(prism_handle* h, const prism_volume* vols, int n_vols, Plan& pl) 
   h->ntiles = static_cast<int>(h->tiles.size());
   if (static_cast<int64_t>(h->ntiles) * TV > (1LL << 31) - 1) return fail(PRISM_E_SHAPE, "too many voxels");
   h->Vpad = h->ntiles * TV;
-  h->Nmax = Nmax;
+  h->Nmax = (Nmax + 3) & ~3;   // rows of the shared-memory table (paired tables pad to 4)
   h->GP = gp;
   h->gp_layout[4 * static_cast<size_t>(n_vols)] = gp;
   h->ypack_len = yoff;
@@ -535,6 +541,8 @@ int init_impl(prism_handle* h, const prism_volume* vols, int n_vols, cudaStream_
   RC(h->alloc(&h->d_vcoord, Vp));
   RC(h->alloc(&h->d_vflag, Vp));
   RC(h->alloc(&h->d_table, h->tab_rows));
+  RC(h->alloc(&h->d_table2, h->tab2_pairs));
+  CK(cudaMemsetAsync(h->d_table2, 0, sizeof(MeasPair) * h->tab2_pairs, st));
   RC(h->alloc(&h->d_gparams, h->GP));
   RC(h->alloc(&h->d_gm, h->GP));
   RC(h->alloc(&h->d_gv, h->GP));
@@ -633,6 +641,7 @@ int init_impl(prism_handle* h, const prism_volume* vols, int n_vols, cudaStream_
     CK(launch_sigma_init(d_part, nbk, Vg, nb0, o.sigma_init, h->d_gparams + gr.gp_off, st));
     CK(launch_pack(h->ia, sig, d_b0, h->d_vox_of_slot, h->vox0[g], gr.tile0, gr.tile0 + gr.ntiles, N, h->d_y, d_bad, st));
     CK(launch_table(d_bv, d_bvec, N, h->d_table + gr.table_off, st));
+    CK(launch_pair_table(h->d_table + gr.table_off, N, h->d_table2 + gr.table2_off, st));
     if (v.init) {
       const float* in = v.init;
       float* tmp_in = nullptr;
@@ -666,7 +675,7 @@ int init_impl(prism_handle* h, const prism_volume* vols, int n_vols, cudaStream_
   // launch geometry of the fused kernel
   const int NW = h->NT / 32;
   h->fused_smem = static_cast<size_t>(h->Nmax) * sizeof(MeasRow) +
-                  static_cast<size_t>(kStages) * kChunk * h->TV * sizeof(float) +
+                  static_cast<size_t>(kStages) * kChunk * (kFusedThreads / h->TPV) * sizeof(float) +
                   (h->cal ? kNGrid * sizeof(float) + static_cast<size_t>(NW) * 2 * h->Nmax * sizeof(float) : 0);
   h->adj_smem = h->cal ? static_cast<size_t>(NW) * 2 * h->Nmax * sizeof(float) : 0;
   if (o.fused) {

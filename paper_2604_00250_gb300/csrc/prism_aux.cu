@@ -62,14 +62,15 @@ __global__ void k_pack(const IterArgs a, const float* __restrict__ sig, const fl
                        float* __restrict__ ypack) {
   const int t = tile_begin + blockIdx.x;
   const Tile tl = a.tiles[t];
-  for (int e = threadIdx.x; e < N * a.TV; e += blockDim.x) {
+  const int NP = (N + 3) & ~3;
+  for (int e = threadIdx.x; e < NP * a.TV; e += blockDim.x) {
     const int n = e / a.TV, vl = e - n * a.TV;
     float val = 0.f;
-    if (vl < tl.count) {
+    if (vl < tl.count && n < N) {
       const int64_t v = vox_of_slot[tl.slot0 + vl] - vox0;
       val = sig[v * N + n] / b0mean[v];
     }
-    ypack[tl.y_off + e] = val;
+    ypack[ypos(tl, n, vl, a.VW)] = val;
   }
 }
 
@@ -96,6 +97,27 @@ __global__ void k_table(const float* bvals, const float* bvecs, int N, MeasRow* 
   r.beta = 0.f;
   r.pad0 = r.pad1 = r.pad2 = 0.f;
   rows[n] = r;
+}
+
+// Paired table of one group (MeasPair), zero past N.
+__global__ void k_pair_table(const MeasRow* rows, int N, int NP, MeasPair* out) {
+  const int pidx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pidx >= NP / 2) return;
+  const float* r0 = reinterpret_cast<const float*>(rows + 2 * pidx);
+  const bool v0 = 2 * pidx < N, v1 = 2 * pidx + 1 < N;
+  float f0[16], f1[16];
+  for (int f = 0; f < 16; ++f) {
+    f0[f] = v0 ? r0[f] : 0.f;
+    f1[f] = v1 ? r0[16 + f] : 0.f;
+  }
+  // field order of MeasRow: gx gy gz nkpar nkperp nkd ecsf egm eres An Bn A beta pad pad pad
+  MeasPair mp;
+  float* o = reinterpret_cast<float*>(&mp);
+  for (int f = 0; f < 16; ++f) {
+    o[2 * f] = f0[f];
+    o[2 * f + 1] = f1[f];
+  }
+  out[pidx] = mp;
 }
 
 __global__ void k_scatter_params(const float* __restrict__ in, const int32_t* __restrict__ slot_of_vox,
@@ -156,7 +178,7 @@ __global__ void k_gather_yhat(const float* __restrict__ ypack, const IterArgs a,
     const int n = e / a.TV, vl = e - n * a.TV;
     if (vl >= tl.count) continue;
     const int64_t v = vox_of_slot[tl.slot0 + vl];
-    out[row_off[v] + n] = ypack[tl.y_off + e];
+    out[row_off[v] + n] = ypack[ypos(tl, n, vl, a.VW)];
   }
 }
 
@@ -435,6 +457,11 @@ cudaError_t launch_pack(const IterArgs& a, const float* sig, const float* b0mean
 }
 cudaError_t launch_table(const float* bvals, const float* bvecs, int N, MeasRow* rows, cudaStream_t st) {
   k_table<<<nblk(N, 128), 128, 0, st>>>(bvals, bvecs, N, rows);
+  return cudaGetLastError();
+}
+cudaError_t launch_pair_table(const MeasRow* rows, int N, MeasPair* out, cudaStream_t st) {
+  const int NP = (N + 3) & ~3;
+  k_pair_table<<<nblk(NP / 2, 128), 128, 0, st>>>(rows, N, NP, out);
   return cudaGetLastError();
 }
 cudaError_t launch_scatter_params(const float* in, const int32_t* sov, int64_t V, int Q, int Vpad, float* th,

@@ -35,6 +35,14 @@ struct __align__(16) MeasRow {
   float beta, pad0, pad1, pad2;  // beta_n
 };
 
+// Paired table: measurements 2p and 2p+1 field-interleaved, so that every field of the
+// pair is one aligned float2 for packed (f32x2) arithmetic. Eight float4 per pair:
+//   {gx, gy} {gz, nkpar} {nkperp, nkd} {ecsf, egm} {eres, An} {Bn, A} {beta, -} {-, -}
+// with each name standing for the float2 (value at 2p, value at 2p+1); rows past N are zero.
+struct __align__(16) MeasPair {
+  float4 q[8];
+};
+
 // A tile: up to TV voxels of one patch, processed by one CTA.
 struct Tile {
   int32_t group, patch, slot0, count;
@@ -53,12 +61,14 @@ struct GroupDev {
   float inv_M;         // 1 / |M_g|
   int32_t calib;       // calibration learned for this group
   int64_t grid_off;    // offset of the group's [nx][ny][nz] slot map
-  int32_t pad[2];
+  int32_t table2_off;  // first MeasPair of the group
+  int32_t pad;
 };
 
 // Kernel arguments shared by the iteration kernels (passed by value).
 struct IterArgs {
   int32_t Q, Vpad, TV, ntiles, Nmax, G;
+  int32_t VW;              // voxels per warp slice of the packed signal (32 / threads per voxel)
   const Tile* tiles;
   const GroupDev* groups;
   const float* y;          // packed b0-normalised signal
@@ -72,6 +82,7 @@ struct IterArgs {
   const uint32_t* vcoord;  // [Vpad] x | y << 10 | z << 20
   const uint32_t* vflag;   // [Vpad] bits 0-5 TV neighbours (+x,-x,+y,-y,+z,-z) masked; bits 8-11 |N(x)|
   const MeasRow* table;    // per-group measurement tables
+  const MeasPair* table2;  // the same, paired (see MeasPair)
   const float* gparams;    // packed group parameters
   float* gU;               // [Vpad] dJ/dU(x)
   float* tile_ab;          // per-tile [2][N] alpha / beta gradient partials
@@ -85,6 +96,18 @@ struct IterArgs {
   float lr, beta1, beta2, eps;
   int32_t nb_priors;       // spatial or directional prior active
 };
+
+// Packed signal layout: a tile's block holds TV / VW warp slices; slice w holds NP x VW
+// floats (NP = N rounded up to a multiple of 4, padding rows zero), so one warp's data
+// for consecutive measurements is one contiguous, 16-byte aligned run.
+// Within a slice, measurements are pair-interleaved: (n, voxel lv) sits at
+// ((n / 2) VW + lv) 2 + n % 2, so one voxel's two measurements of a pair are one float2.
+__device__ __forceinline__ size_t ypos(const Tile& tl, int n, int vl, int VW) {
+  const int w = vl / VW;
+  const int NP = (tl.n_meas + 3) & ~3;
+  return static_cast<size_t>(tl.y_off) + static_cast<size_t>(w) * NP * VW +
+         (static_cast<size_t>(n >> 1) * VW + (vl - w * VW)) * 2 + (n & 1);
+}
 
 // Auxiliary arguments of the unfused (plain) kernels.
 struct PlainArgs {

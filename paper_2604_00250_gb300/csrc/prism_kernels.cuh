@@ -324,6 +324,112 @@ __device__ __forceinline__ void fiber_weights(const Vox<K>& P, float (&ffin)[K],
   }
 }
 
+// ---------------------------------------------------------------------------
+// Packed path (one thread per voxel, MSE, no calibration): two measurements per step in
+// f32x2 arithmetic. Voxel constants are held duplicated; accumulators are float2 and are
+// folded after the loop. The residual is taken as y - y_hat (signs restored when folding).
+// ---------------------------------------------------------------------------
+template <int K>
+struct VoxP {
+  float2 fcsf, fgm, fres, nS0, fin, omf;
+  float2 d[K][3];
+  float2 ffin[K], fomf[K];
+};
+
+template <int K>
+struct AccP {
+  float2 gcsf, ggm, gres, l1;
+  float2 gwa[K], gwb[K];
+  float2 gd[K][3];
+};
+
+__device__ __forceinline__ float2 dup2(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float2 lo2(const float4& v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(const float4& v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float2 ex2_2(float2 v) { return make_float2(ex2f_(v.x), ex2f_(v.y)); }
+
+template <int K>
+__device__ __forceinline__ void voxp_init(const Vox<K>& P, VoxP<K>& D, AccP<K>& A) {
+  D.fcsf = dup2(P.f[0]);
+  D.fgm = dup2(P.f[1]);
+  D.fres = dup2(P.f[K + 2]);
+  D.nS0 = dup2(-P.S0);
+  D.fin = dup2(P.fin);
+  D.omf = dup2(P.omf);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) D.d[k][c] = dup2(P.d[k][c]);
+    D.ffin[k] = dup2(P.f[2 + k] * P.fin);
+    D.fomf[k] = dup2(P.f[2 + k] * P.omf);
+  }
+  const float2 z = make_float2(0.f, 0.f);
+  A.gcsf = A.ggm = A.gres = A.l1 = z;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    A.gwa[k] = A.gwb[k] = z;
+    A.gd[k][0] = A.gd[k][1] = A.gd[k][2] = z;
+  }
+}
+
+// One packed step over measurements (2p, 2p+1). With MASK, lanes whose msk is 0 add nothing.
+template <int K, bool MASK>
+__device__ __forceinline__ void step2(const VoxP<K>& D, const MeasPair& R, float2 y, float2 msk, AccP<K>& A) {
+  const float4 q0 = R.q[0], q1 = R.q[1], q2 = R.q[2], q3 = R.q[3], q4 = R.q[4], q5 = R.q[5];
+  const float2 gx = lo2(q0), gy = hi2(q0), gz = lo2(q1), nkpar = hi2(q1);
+  const float2 nkperp = lo2(q2), nkd = hi2(q2), ecsf = lo2(q3), egm = hi2(q3);
+  const float2 eres = lo2(q4), An = hi2(q4), Bn = lo2(q5);
+  float2 T = __fmul2_rn(D.fcsf, ecsf);
+  T = __ffma2_rn(D.fgm, egm, T);
+  T = __ffma2_rn(D.fres, eres, T);
+  float2 c[K], e1[K], p[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    c[k] = __ffma2_rn(D.d[k][0], gx, __ffma2_rn(D.d[k][1], gy, __fmul2_rn(D.d[k][2], gz)));
+    const float2 c2 = __fmul2_rn(c[k], c[k]);
+    e1[k] = ex2_2(__fmul2_rn(nkpar, c2));
+    p[k] = ex2_2(__ffma2_rn(nkd, c2, nkperp));
+    T = __ffma2_rn(D.ffin[k], e1[k], __ffma2_rn(D.fomf[k], p[k], T));
+  }
+  float2 r = __ffma2_rn(D.nS0, T, y);   // y - y_hat
+  if (MASK) r = __fmul2_rn(r, msk);
+  A.l1 = __ffma2_rn(r, r, A.l1);
+  A.gcsf = __ffma2_rn(r, ecsf, A.gcsf);
+  A.ggm = __ffma2_rn(r, egm, A.ggm);
+  A.gres = __ffma2_rn(r, eres, A.gres);
+  const float2 anf = __fmul2_rn(An, D.fin), bno = __fmul2_rn(Bn, D.omf);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    A.gwa[k] = __ffma2_rn(r, e1[k], A.gwa[k]);
+    A.gwb[k] = __ffma2_rn(r, p[k], A.gwb[k]);
+    const float2 inner = __ffma2_rn(bno, p[k], __fmul2_rn(anf, e1[k]));
+    const float2 w = __fmul2_rn(__fmul2_rn(r, c[k]), inner);
+    A.gd[k][0] = __ffma2_rn(w, gx, A.gd[k][0]);
+    A.gd[k][1] = __ffma2_rn(w, gy, A.gd[k][1]);
+    A.gd[k][2] = __ffma2_rn(w, gz, A.gd[k][2]);
+  }
+}
+
+// Fold packed accumulators into the scalar ones (dJ/dS0 from the compartment sums:
+// sum_n q T = f_csf sum q E_csf + ... + sum_k (f_k f_in sum q e1 + f_k (1-f_in) sum q p)).
+template <int K>
+__device__ __forceinline__ void accp_fold(const Vox<K>& P, const AccP<K>& B, Acc<K>& A) {
+  A.gcsf = -(B.gcsf.x + B.gcsf.y);
+  A.ggm = -(B.ggm.x + B.ggm.y);
+  A.gres = -(B.gres.x + B.gres.y);
+  A.l1 = B.l1.x + B.l1.y;
+  float g = P.f[0] * A.gcsf + P.f[1] * A.ggm + P.f[K + 2] * A.gres;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    A.gwa[k] = -(B.gwa[k].x + B.gwa[k].y);
+    A.gwb[k] = -(B.gwb[k].x + B.gwb[k].y);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) A.gd[k][c] = -(B.gd[k][c].x + B.gd[k][c].y);
+    g = fmaf(P.f[2 + k] * P.fin, A.gwa[k], fmaf(P.f[2 + k] * P.omf, A.gwb[k], g));
+  }
+  A.gS0 = g;
+}
+
 // Scaled data-term gradient w.r.t. transformed parameters.
 template <int K>
 __device__ __forceinline__ void data_grad(const Vox<K>& P, const Acc<K>& A, float scale, float& gS0,
@@ -374,106 +480,110 @@ __device__ __forceinline__ void block_reduce3(double v0, double v1, double v2, d
 // Fused iteration: one persistent kernel over the tile queue does synthesis,
 // calibration, data term, adjoint, priors, chain rule and the voxel Adam update.
 //
-// The tile's packed signal block ([N][TV] floats, contiguous) streams through a
-// ring of kStages shared-memory buffers of kChunk measurements each, filled by bulk
-// TMA copies (cp.async.bulk) issued by thread 0 and tracked by full / empty
-// mbarriers, so the hot loop reads y from shared memory. The measurement table and
-// the bias grid arrive the same way whenever the group changes.
+// Each warp streams the signal of its own VW voxels (a contiguous [NP][VW] slice of
+// the tile's packed block) through a private ring of kStages shared-memory buffers of
+// kChunk measurements, refilled by its lane 0 with bulk TMA copies (cp.async.bulk)
+// tracked by per-stage mbarriers. The stream runs across tile boundaries: while a
+// warp finishes a tile it already fetches the first chunks of the CTA's next tile.
+// The measurement table and the bias grid arrive by bulk copy when the group changes.
 // ===========================================================================
 constexpr int kChunk = 16;    // measurements per ring stage
-constexpr int kStages = 4;    // ring depth
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
+constexpr int kStages = 4;    // ring depth per warp
+constexpr int kFusedThreads = 128;
 
 template <int K, int TPV, int LOSS, bool CAL>
-__global__ void __launch_bounds__(128, 4) k_iter_fused(const IterArgs a) {
+__global__ void __launch_bounds__(kFusedThreads, 4) k_iter_fused(const IterArgs a) {
   constexpr int NF = K + 3, Q = 4 * K + 5, XF = 4 * K + 3;
+  constexpr int NW = kFusedThreads / 32;
+  constexpr int VW = 32 / TPV;              // voxels per warp
+  constexpr bool PACKED = (TPV == 1) && (LOSS == kLossMSE) && !CAL;
   static_assert(kChunk % TPV == 0, "chunk must split evenly across the voxel's lanes");
   extern __shared__ __align__(16) unsigned char smem[];
-  const int TV = a.TV, Vp = a.Vpad;
+  const int Vp = a.Vpad;
   MeasRow* s_tab = reinterpret_cast<MeasRow*>(smem);
-  float* s_ring = reinterpret_cast<float*>(s_tab + a.Nmax);           // [kStages][kChunk][TV]
-  float* s_blr = s_ring + kStages * kChunk * TV;                        // [512] (calibration)
-  float* s_ab = s_blr + (CAL ? kNGrid : 0);                             // [NW][2][Nmax] (calibration)
+  float* s_ring = reinterpret_cast<float*>(s_tab + a.Nmax);                 // [NW][kStages][kChunk][VW]
+  float* s_blr = s_ring + NW * kStages * kChunk * VW;                       // [512] (calibration)
+  float* s_ab = s_blr + (CAL ? kNGrid : 0);                                 // [NW][2][Nmax] (calibration)
   __shared__ uint64_t s_bar;                 // table / bias grid
-  __shared__ uint64_t s_full[kStages];
-  __shared__ uint64_t s_empty[kStages];
-  __shared__ int s_tile;
+  __shared__ uint64_t s_full[NW][kStages];
+  __shared__ int s_first, s_next;
   __shared__ double s_red[8][3];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int NW = blockDim.x >> 5;
-  const int vl = tid / TPV, js = tid % TPV;
+  const int vl = tid / TPV, js = tid % TPV, lv = lane / TPV;
   const int step = *a.step;
   const int par = step & 1;
   const float* xf_cur = a.xf + static_cast<size_t>(par) * XF * Vp;
   float* xf_nxt = a.xf + static_cast<size_t>(par ^ 1) * XF * Vp;
+  float* ring = s_ring + warp * (kStages * kChunk * VW);
   if (tid == 0) {
     mbar_init(&s_bar, 1);
-    for (int s = 0; s < kStages; ++s) {
-      mbar_init(&s_full[s], 1);
-      mbar_init(&s_empty[s], NW);
-    }
+    for (int w = 0; w < NW; ++w)
+      for (int s = 0; s < kStages; ++s) mbar_init(&s_full[w][s], 1);
     fence_mbar_init();
+    s_first = atomicAdd(a.queue, 1);
   }
   __syncthreads();
   const float stepsz = a.adamc[0], isbc2 = a.adamc[1];
   int cur_group = -1;
   uint32_t tphase = 0;
-  uint32_t gchunk = 0;   // ring chunks consumed by this CTA so far
+  uint32_t g = 0;      // stream chunks consumed by this warp
+  uint32_t iss = 0;    // stream chunks issued by this warp (lane 0's copy is authoritative)
+  uint32_t base = 0;   // stream position of the current tile's chunk 0
   bool failed = false;
+  int t = s_first;
 
-  // Thread 0: copy chunk j of the tile's signal block into ring slot of global chunk g.
-  auto issue = [&](uint32_t g, const float* ysrc, int j, int N) {
-    const int s = g % kStages;
-    const uint32_t use = g / kStages;
-    if (use >= 1 && !failed) {
-      if (!mbar_wait(&s_empty[s], (use - 1) & 1)) {
-        atomicOr(a.status, kStTimeout);
-        failed = true;
-      }
-    }
-    const int cnt = min(kChunk, N - j * kChunk);
-    const uint32_t bytes = static_cast<uint32_t>(cnt) * TV * 4u;
+  // Lane 0: issue stream position `pos` = chunk j of the tile at y_off (NP padded rows).
+  auto issue = [&](uint32_t pos, int64_t y_off, int NP, int j) {
+    const int s = pos % kStages;
+    const int cnt = min(kChunk, NP - j * kChunk);
+    const uint32_t bytes = static_cast<uint32_t>(cnt) * VW * 4u;
+    const float* src = a.y + y_off + static_cast<int64_t>(warp) * NP * VW + static_cast<int64_t>(j) * kChunk * VW;
     fence_proxy_async_smem();
-    mbar_expect_tx(&s_full[s], bytes);
-    tma_bulk_g2s(s_ring + static_cast<size_t>(s) * kChunk * TV, ysrc + static_cast<size_t>(j) * kChunk * TV,
-                 bytes, &s_full[s]);
+    mbar_expect_tx(&s_full[warp][s], bytes);
+    tma_bulk_g2s(ring + s * (kChunk * VW), src, bytes, &s_full[warp][s]);
   };
 
-  for (;;) {
-    if (tid == 0) s_tile = atomicAdd(a.queue, 1);
+  while (t < a.ntiles) {
+    if (tid == 0) s_next = atomicAdd(a.queue, 1);
     __syncthreads();
-    const int t = s_tile;
-    if (t >= a.ntiles) break;
-    if (__syncthreads_or(failed)) break;   // block-uniform exit after a timed-out wait
+    const int t_next = s_next;
     const Tile tl = a.tiles[t];
     const GroupDev gr = a.groups[tl.group];
-    const int N = tl.n_meas;
-    const int nch = (N + kChunk - 1) / kChunk;
-    const float* __restrict__ ysrc = a.y + tl.y_off;
+    const int N = tl.n_meas, NP = (N + 3) & ~3;
+    const int nch = (NP + kChunk - 1) / kChunk;
+    int64_t ny_off = 0;
+    int nNP = 0, nnch = 0;
+    if (t_next < a.ntiles) {
+      const Tile tn = a.tiles[t_next];
+      ny_off = tn.y_off;
+      nNP = (tn.n_meas + 3) & ~3;
+      nnch = (nNP + kChunk - 1) / kChunk;
+    }
     if (tl.group != cur_group) {
       if (tid == 0) {
         fence_proxy_async_smem();
-        const uint32_t tb = static_cast<uint32_t>(N * sizeof(MeasRow));
-        mbar_expect_tx(&s_bar, tb + (CAL ? kNGrid * 4u : 0u));
-        tma_bulk_g2s(s_tab, a.table + gr.table_off, tb, &s_bar);
-        if (CAL) tma_bulk_g2s(s_blr, a.gparams + gr.gp_off + 4 + 2 * gr.N4, kNGrid * 4u, &s_bar);
+        if (PACKED) {
+          const uint32_t tb = static_cast<uint32_t>(NP / 2 * sizeof(MeasPair));
+          mbar_expect_tx(&s_bar, tb);
+          tma_bulk_g2s(s_tab, a.table2 + gr.table2_off, tb, &s_bar);
+        } else {
+          const uint32_t tb = static_cast<uint32_t>(N * sizeof(MeasRow));
+          mbar_expect_tx(&s_bar, tb + (CAL ? kNGrid * 4u : 0u));
+          tma_bulk_g2s(s_tab, a.table + gr.table_off, tb, &s_bar);
+          if (CAL) tma_bulk_g2s(s_blr, a.gparams + gr.gp_off + 4 + 2 * gr.N4, kNGrid * 4u, &s_bar);
+        }
       }
-      if (!mbar_wait(&s_bar, tphase)) {
+      if (!failed && !mbar_wait(&s_bar, tphase)) {
         if (tid == 0) atomicOr(a.status, kStTimeout);
         failed = true;
       }
       tphase ^= 1;
       cur_group = tl.group;
     }
-    // prologue: the first kStages - 1 chunks of this tile, and an L2 prefetch of the rows
-    // the epilogue reads (parameters, Adam moments, neighbour-prior data of the tile)
-    if (tid == 0) {
-      for (int j = 0; j < kStages - 1 && j < nch; ++j) issue(gchunk + j, ysrc, j, N);
-      const uint32_t rb = static_cast<uint32_t>(TV) * 4u;
+    // L2 prefetch of the rows the epilogue reads (parameters, Adam moments, prior data)
+    if (tid == 32) {
+      const uint32_t rb = static_cast<uint32_t>(kFusedThreads / TPV) * 4u;
       for (int q = 0; q < Q; ++q) {
         const size_t o = static_cast<size_t>(q) * Vp + tl.slot0;
         prefetch_l2(a.theta + o, rb);
@@ -511,39 +621,79 @@ __global__ void __launch_bounds__(128, 4) k_iter_fused(const IterArgs a) {
     acc_zero<K>(A);
     float ffin[K], fomf[K];
     fiber_weights<K>(P, ffin, fomf);
+    VoxP<K> DP;
+    AccP<K> AP;
+    if constexpr (PACKED) voxp_init<K>(P, DP, AP);
     for (int j = 0; j < nch; ++j) {
-      const uint32_t g = gchunk + j;
-      if (tid == 0 && j + kStages - 1 < nch) issue(g + kStages - 1, ysrc, j + kStages - 1, N);
+      if (lane == 0) {
+        // keep kStages chunks of this warp's stream in flight (this tile, then the next)
+        while (iss < g + kStages) {
+          const uint32_t r = iss - base;
+          if (r < static_cast<uint32_t>(nch)) issue(iss, tl.y_off, NP, r);
+          else if (r - nch < static_cast<uint32_t>(nnch)) issue(iss, ny_off, nNP, r - nch);
+          else break;
+          ++iss;
+        }
+      }
       const int s = g % kStages;
-      if (!failed && !mbar_wait(&s_full[s], (g / kStages) & 1)) {
+      if (!failed && !mbar_wait(&s_full[warp][s], (g / kStages) & 1)) {
         atomicOr(a.status, kStTimeout);
         failed = true;
       }
-      const float* __restrict__ yc = s_ring + static_cast<size_t>(s) * kChunk * TV;
-      const int nb = j * kChunk;
-      const int cnt = min(kChunk, N - nb);
-#pragma unroll 4
-      for (int i = 0; i < kChunk / TPV; ++i) {
-        const int nl = i * TPV + js;
-        const bool ok = act && (nl < cnt);
-        float rr = 0.f, u = 0.f;
-        if (ok) {
-          const MeasRow R = s_tab[nb + nl];
-          pair<K, LOSS, CAL, false>(P, ffin, fomf, R, yc[nl * TV + vl], B, inv_s2, 0.f, A, rr, u);
+      const int cnt = min(kChunk, N - j * kChunk);
+      if constexpr (PACKED) {
+        const float2* __restrict__ yc2 = reinterpret_cast<const float2*>(ring + s * (kChunk * VW)) + lv;
+        const MeasPair* __restrict__ tab2 = reinterpret_cast<const MeasPair*>(s_tab) + j * (kChunk / 2);
+        if (act && cnt == kChunk) {
+#pragma unroll
+          for (int i = 0; i < kChunk / 2; ++i) step2<K, false>(DP, tab2[i], yc2[i * VW], make_float2(1.f, 1.f), AP);
+        } else if (act) {
+          for (int i = 0; i < (cnt + 1) / 2; ++i)
+            step2<K, true>(DP, tab2[i], yc2[i * VW], make_float2(1.f, (2 * i + 1 < cnt) ? 1.f : 0.f), AP);
         }
-        if (CAL) {
-          float su = warp_sum_range<TPV, 16>(ok ? u : 0.f);
-          float sr = warp_sum_range<TPV, 16>(ok ? rr : 0.f);
-          if (lane < TPV && nl < cnt) {
-            s_ab[(warp * 2) * a.Nmax + nb + nl] = su;
-            s_ab[(warp * 2 + 1) * a.Nmax + nb + nl] = sr;
+        __syncwarp();
+        ++g;
+        continue;
+      }
+      // pair-interleaved slice: chunk-relative measurement nl of voxel lv
+      const float* __restrict__ yc = ring + s * (kChunk * VW) + 2 * lv;
+      const MeasRow* __restrict__ tab = s_tab + j * kChunk;
+      if (!CAL && act && cnt == kChunk) {
+        // full chunk: no predicates
+#pragma unroll
+        for (int i = 0; i < kChunk / TPV; ++i) {
+          const int nl = i * TPV + js;
+          float rr, u;
+          pair<K, LOSS, CAL, false>(P, ffin, fomf, tab[nl], yc[(nl >> 1) * (2 * VW) + (nl & 1)], B, inv_s2, 0.f, A, rr, u);
+        }
+      } else {
+#pragma unroll 4
+        for (int i = 0; i < kChunk / TPV; ++i) {
+          const int nl = i * TPV + js;
+          const bool ok = act && (nl < cnt);
+          float rr = 0.f, u = 0.f;
+          if (ok) pair<K, LOSS, CAL, false>(P, ffin, fomf, tab[nl], yc[(nl >> 1) * (2 * VW) + (nl & 1)], B, inv_s2, 0.f, A, rr, u);
+          if (CAL) {
+            float su = warp_sum_range<TPV, 16>(ok ? u : 0.f);
+            float sr = warp_sum_range<TPV, 16>(ok ? rr : 0.f);
+            if (lane < TPV && nl < cnt) {
+              s_ab[(warp * 2) * a.Nmax + j * kChunk + nl] = su;
+              s_ab[(warp * 2 + 1) * a.Nmax + j * kChunk + nl] = sr;
+            }
           }
         }
       }
       __syncwarp();
-      if (lane == 0) mbar_arrive(&s_empty[s]);
+      ++g;
     }
-    gchunk += nch;
+    base += nch;
+    // voxel transforms again (not kept live across the loop)
+    {
+      float th[Q];
+      load_theta<K>(a.theta, Vp, slot, act, th);
+      transform<K>(th, P);
+    }
+    if constexpr (PACKED) accp_fold<K>(P, AP, A);
     acc_reduce_tpv<K, TPV>(A);
 
     // ---- data-term gradient and value
@@ -566,16 +716,16 @@ __global__ void __launch_bounds__(128, 4) k_iter_fused(const IterArgs a) {
     // ---- chain rule and Adam (raw parameters re-read: they are not kept live across the loop)
     float th[Q];
     load_theta<K>(a.theta, Vp, slot, act, th);
-    float g[Q];
-    chain_raw<K>(P, gS0, gf, gd, gfin, g);
+    float gq[Q];
+    chain_raw<K>(P, gS0, gf, gd, gfin, gq);
     const bool writer = act && (js == 0);
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       const size_t ix = static_cast<size_t>(q) * Vp + slot;
       float mq = writer ? a.m[ix] : 0.f;
       float vq = writer ? a.v[ix] : 0.f;
-      mq = fmaf(a.beta1, mq, (1.f - a.beta1) * g[q]);
-      vq = fmaf(a.beta2, vq, (1.f - a.beta2) * g[q] * g[q]);
+      mq = fmaf(a.beta1, mq, (1.f - a.beta1) * gq[q]);
+      vq = fmaf(a.beta2, vq, (1.f - a.beta2) * gq[q] * gq[q]);
       th[q] -= stepsz * mq / fmaf(sqrtf(vq), isbc2, a.eps);
       if (writer) {
         a.m[ix] = mq;
@@ -593,7 +743,7 @@ __global__ void __launch_bounds__(128, 4) k_iter_fused(const IterArgs a) {
     block_reduce3(writer ? static_cast<double>(dloss) : 0.0, writer ? static_cast<double>(dsig) : 0.0,
                   writer ? static_cast<double>(ploss) : 0.0, s_red, a.tile_red + 4 * static_cast<size_t>(t));
     if (CAL) {
-      for (int e = tid; e < 2 * N; e += blockDim.x) {
+      for (int e = tid; e < 2 * N; e += kFusedThreads) {
         const int w2 = (e < N) ? 0 : 1;
         const int n = e - w2 * N;
         float sum = 0.f;
@@ -601,11 +751,12 @@ __global__ void __launch_bounds__(128, 4) k_iter_fused(const IterArgs a) {
         a.tile_ab[tl.ab_off + e] = sum * scale;
       }
     }
-    __syncthreads();
+    if (__syncthreads_or(failed)) break;   // block-uniform exit after a timed-out wait
+    t = t_next;
   }
-  if (failed && tid == 0) {
-    // let any copy still in flight land before the CTA's shared memory is released
-    for (int s = 0; s < kStages; ++s) mbar_wait(&s_full[s], 0), mbar_wait(&s_full[s], 1);
+  if (failed && lane == 0) {
+    // let copies still in flight land before the CTA's shared memory is released
+    for (uint32_t p = g; p < iss; ++p) mbar_wait(&s_full[warp][p % kStages], (p / kStages) & 1);
   }
   // The last CTA to leave resets the queue for the next iteration.
   if (tid == 0) {
@@ -672,7 +823,7 @@ __global__ void __launch_bounds__(256) k_synth(const IterArgs a, const PlainArgs
       T = fmaf(P.f[2 + k], fmaf(P.fin, e1, P.omf * p), T);
     }
     const float S = P.S0 * T;
-    pa.yhat[tl.y_off + static_cast<size_t>(n) * a.TV + vl] = CAL ? fmaf(R.A * B, S, R.beta) : S;
+    pa.yhat[ypos(tl, n, vl, a.VW)] = CAL ? fmaf(R.A * B, S, R.beta) : S;
   }
 }
 
@@ -695,7 +846,7 @@ __global__ void __launch_bounds__(256) k_loss(const IterArgs a, const PlainArgs 
   for (int e = threadIdx.x; e < N * a.TV; e += blockDim.x) {
     const int n = e / a.TV, vl = e - n * a.TV;
     if (vl >= tl.count) continue;
-    const size_t ix = tl.y_off + e;
+    const size_t ix = ypos(tl, n, vl, a.VW);
     const float yh = pa.yhat[ix], yv = a.y[ix];
     float rr;
     if (LOSS == kLossMSE) {
@@ -758,7 +909,7 @@ __global__ void __launch_bounds__(256) k_adjoint(const IterArgs a, const PlainAr
     const bool ok = act && (n < N);
     float rr = 0.f, u = 0.f;
     if (ok) {
-      const size_t ix = tl.y_off + static_cast<size_t>(n) * a.TV + vl;
+      const size_t ix = ypos(tl, n, vl, a.VW);
       pair<K, kLossMSE, CAL, true>(P, ffin, fomf, tab[n], 0.f, B, 0.f, pa.r[ix], A, rr, u);
     }
     if (CAL) {

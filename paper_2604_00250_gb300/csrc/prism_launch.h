@@ -58,6 +58,7 @@ cudaError_t launch_pack(const IterArgs& a, const float* sig, const float* b0mean
                         int64_t vox0, int tile_begin, int tile_end, int N, float* ypack, int* bad,
                         cudaStream_t st);
 cudaError_t launch_table(const float* bvals, const float* bvecs, int N, MeasRow* rows, cudaStream_t st);
+cudaError_t launch_pair_table(const MeasRow* rows, int N, MeasPair* out, cudaStream_t st);
 cudaError_t launch_scatter_params(const float* in, const int32_t* slot_of_vox, int64_t V, int Q, int Vpad,
                                   float* theta, cudaStream_t st);
 cudaError_t launch_gather_params(const float* theta, const int32_t* slot_of_vox, int64_t V, int Q, int Vpad,

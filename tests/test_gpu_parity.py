@@ -99,15 +99,17 @@ def test_forward_and_gradient(loss, cal, K, tpv, extra):
     f.close()
 
 
-@pytest.mark.parametrize("fused", [1, 0])
-@pytest.mark.parametrize("loss,cal", [("mse", False), ("nll", True)])
-def test_adam_steps_match_oracle(fused, loss, cal):
-    """Three iterations (objective, gradient, Adam) on the fused and the plain path."""
+@pytest.mark.parametrize("fused,tpv", [(1, 1), (1, 4), (1, 16), (0, 1), (0, 4)])
+@pytest.mark.parametrize("loss,cal", [("mse", False), ("nll", True), ("nll", False), ("mse", True)])
+def test_adam_steps_match_oracle(fused, tpv, loss, cal):
+    """Three iterations (objective, gradient, Adam) on the fused path (packed two-measurement
+    steps for one thread per voxel with MSE and no calibration) and the plain path; one volume
+    has an odd measurement count (21), so masked partial chunks and pairs are exercised."""
     vols = _problem(cal)
     K = 3
     inits = inits_for(vols, K, 5)
     kw = dict(K=K, loss=loss, calibration=cal, patch_dim=4, lam_sp=0.01, lam_dir=0.005, fused=fused,
-              use_graph=fused)
+              use_graph=fused, threads_per_voxel=tpv)
     f, ovs = make_pair(vols, inits, **kw)
     f.step(3)
     f.sync()
@@ -121,13 +123,14 @@ def test_adam_steps_match_oracle(fused, loss, cal):
     f.close()
 
 
-def test_fit_crossing_patch_200_iterations():
+@pytest.mark.parametrize("tpv", [16, 1])
+def test_fit_crossing_patch_200_iterations(tpv):
     """One 8^3 patch of crossings, 96 measurements, MSE, 200 Adam iterations: median
     matched angular deviation <= 0.5 deg and identical peak counts per voxel."""
     vol = P.crossing_patch(0)
     K = 3
     th0 = P.default_init(vol.n_vox, K, 0)
-    f, ovs = make_pair([vol], [th0], K=K, patch_dim=8)
+    f, ovs = make_pair([vol], [th0], K=K, patch_dim=8, threads_per_voxel=tpv)
     f.step(200)
     f.sync()
     th_gpu = f.params_host()
@@ -139,11 +142,12 @@ def test_fit_crossing_patch_200_iterations():
     f.close()
 
 
-def test_fused_is_deterministic_and_resumable():
-    vols = _problem(True)
+@pytest.mark.parametrize("loss,cal,tpv", [("nll", True, 0), ("mse", False, 1)])
+def test_fused_is_deterministic_and_resumable(loss, cal, tpv):
+    vols = _problem(cal)
     K = 3
     inits = inits_for(vols, K, 9)
-    kw = dict(K=K, loss="nll", calibration=True, patch_dim=4, lam_sp=0.01, lam_dir=0.005)
+    kw = dict(K=K, loss=loss, calibration=cal, patch_dim=4, lam_sp=0.01, lam_dir=0.005, threads_per_voxel=tpv)
     f1, _ = make_pair(vols, inits, **kw)
     f1.step(6)
     blob = f1.state()
