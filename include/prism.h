@@ -5,14 +5,14 @@
  * Synthesis for Fixel Recovery in Diffusion MRI") fits, per voxel x of a brain
  * mask and measurement n (b-value b_n, unit gradient g_n), the forward model
  *
- *   S(x,n)    = S0 (f_csf E_csf + f_gm E_gm + sum_k f_wm,k E_wm,k + f_res E_res)   Sec. 2.2, Eq. 2
- *   E_iso     = exp(-b D_iso), D = 3.0 / 0.9 / 0.2 x 1e-3 mm^2/s                   Sec. 2.2, Eq. 3
+ *   S(x,n)    = S0 (f_csf E_csf + f_gm E_gm + sum_k f_wm,k E_wm,k + f_res E_res)   Sec. 2.2, Eq. 3
+ *   E_iso     = exp(-b D_iso), D = 3.0 / 0.9 / 0.2 x 1e-3 mm^2/s                   Sec. 2.2, Eq. 4
  *   E_wm,k    = f_in e^{-b D_par c^2} + (1-f_in) e^{-b (D_par c^2 + D_perp (1-c^2))},
- *               c = d_k . g_n, D_par = 1.7e-3, D_perp = 0.4e-3                     Sec. 2.2, Eq. 4
- *   y_hat     = exp(alpha_n) B(x) S(x,n) + beta_n, B = exp(trilinear(b_lr 8^3))    Sec. 2.3, Eq. 5
+ *               c = d_k . g_n, D_par = 1.7e-3, D_perp = 0.4e-3                     Sec. 2.2, Eq. 5
+ *   y_hat     = exp(alpha_n) B(x) S(x,n) + beta_n, B = exp(trilinear(b_lr 8^3))    Sec. 2.3, Eq. 6
  *
- * to b0-normalised data y (Sec. 2.5) by minimising the MSE (Eq. 7) or the
- * Rician NLL with learned sigma = exp(sigma_log) (Eq. 8), plus the priors of
+ * to b0-normalised data y (Sec. 2.5) by minimising the MSE (Eq. 8) or the
+ * Rician NLL with learned sigma = exp(sigma_log) (Eq. 9), plus the priors of
  * Sec. 2.4, with Adam (the Table 2 comparator). Each iteration computes the
  * objective, its exact gradient (hand-written adjoint) and one Adam update of
  * every parameter.
@@ -75,13 +75,13 @@ typedef struct prism_volume {
 
 typedef struct prism_options {
   int32_t K;              /* fibers per voxel, 1..5 */
-  int32_t loss;           /* PRISM_LOSS_MSE (Eq. 7) or PRISM_LOSS_NLL (Eq. 8) */
+  int32_t loss;           /* PRISM_LOSS_MSE (Eq. 8) or PRISM_LOSS_NLL (Eq. 9) */
   int32_t calibration;    /* 1: learn bias field + per-measurement affine (Sec. 2.3) */
   int32_t patch_dim;      /* spatial patch edge, 1..64; neighbour priors stay inside a patch */
   float lam_rep;          /* direction repulsion weight (Sec. 2.4), 0.01 */
   float lam_sparse;       /* L1 on minor fiber fractions, 0.02 */
   float tau;              /* minor-fraction threshold, 0.15 */
-  float lam_sp;           /* Huber-Laplacian fraction smoothness (Eq. 6), 0 = off (paper default 0.01) */
+  float lam_sp;           /* Huber-Laplacian fraction smoothness (Eq. 7), 0 = off (paper default 0.01) */
   float huber_delta;      /* Huber transition, 0.05 */
   float lam_dir;          /* directional continuity, 0 = off (paper 0.005) */
   float w_alpha, w_beta, w_blr, w_tv, tv_eps; /* calibration regularisers: 1e-3 each, eps 1e-6 */
@@ -208,7 +208,7 @@ int prism_fit(const prism_volume* vols, int32_t n_vols, const prism_options* opt
  * routine: beyond the caller's buffers it uses one fixed 128 KiB array inside the
  * library, which every GPU that loads the library keeps until the process exits.
  *
- * Evaluates, for n_vox voxels forming one group, J = MSE data term (Eq. 7, divided by
+ * Evaluates, for n_vox voxels forming one group, J = MSE data term (Eq. 8, divided by
  * n_vox) + lam_rep * mean repulsion + lam_sparse * mean sparsity (Sec. 2.4), without
  * calibration or neighbour priors, on raw signal rows that it b0-normalises itself
  * (mean of the b <= 50 measurements), and its gradient -- the same values prism_forward

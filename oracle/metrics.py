@@ -1,10 +1,10 @@
 """Peak extraction and angular comparison -- TEST INFRASTRUCTURE ONLY.
 
-Fiber directions are used directly as peaks (Sec. 4 "Configuration"); a fiber
+Fiber directions are used directly as peaks (Sec. 3 "Configuration"); a fiber
 counts as a peak when its share of the white-matter fraction is at least
 `rel_thresh` (reading R20). Angles are arccos|d . d'| in degrees (directions
 are sign-free). Best-match angular error matches each reference fiber to its
-closest predicted fiber (Sec. 4 "Tracking & metrics").
+closest predicted fiber (Sec. 3 "Tracking & metrics").
 """
 import itertools
 

@@ -8,15 +8,15 @@ It is the plain, slow definition of one PRISM fit (Abouagour et al., "PRISM:
 Differentiable Analysis-by-Synthesis for Fixel Recovery in Diffusion MRI"),
 in float64 PyTorch CPU ops, following the paper in order:
 
-  * tissue model, Sec. 2.2 Eqs. 2-4 (S, E_iso, stick-and-zeppelin E_wm),
+  * tissue model, Sec. 2.2 Eqs. 3-5 (S, E_iso, stick-and-zeppelin E_wm),
   * per-voxel parameterisation, Sec. 2.2 "Per-voxel parameters" and Sec. 2.5
     "Constraints and solver" (softplus S0, softmax fractions, sigmoid f_intra,
     l2-normalised directions),
-  * calibration chain, Sec. 2.3 Eq. 5 (bias field exp(upsample(b_lr)),
+  * calibration chain, Sec. 2.3 Eq. 6 (bias field exp(upsample(b_lr)),
     per-measurement exp(alpha_n) and beta_n, sigma = exp(sigma_log)),
-  * data terms, Sec. 2.5 Eq. 7 (MSE) and Eq. 8 (Rician NLL), on b0-normalised
+  * data terms, Sec. 2.5 Eq. 8 (MSE) and Eq. 9 (Rician NLL), on b0-normalised
     signals (Sec. 2.5, first paragraph),
-  * priors, Sec. 2.4 (Huber-Laplacian Eq. 6, repulsion, L1 sparsity,
+  * priors, Sec. 2.4 (Huber-Laplacian Eq. 7, repulsion, L1 sparsity,
     directional continuity, calibration L2 and TV),
   * total objective, Sec. 2.5 (L_data + sum_i lambda_i R_i + R_cal),
   * Adam (the paper's Table 2 comparator; Kingma & Ba 2015, Algorithm 1).
@@ -73,12 +73,12 @@ NBR6 = ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1))
 @dataclass
 class Options:
     K: int = 3
-    loss: str = "mse"                  # "mse" (Eq. 7) or "nll" (Eq. 8)
+    loss: str = "mse"                  # "mse" (Eq. 8) or "nll" (Eq. 9)
     calibration: bool = False          # Sec. 2.3 bias + affine
     lam_rep: float = 0.01              # Sec. 2.4 topology priors
     lam_sparse: float = 0.02
     tau: float = 0.15
-    lam_sp: float = 0.0                # Huber-Laplacian (Eq. 6), default 0.01 when on
+    lam_sp: float = 0.0                # Huber-Laplacian (Eq. 7), default 0.01 when on
     huber_delta: float = 0.05
     lam_dir: float = 0.0               # directional continuity, 0.005 when on
     w_alpha: float = 1e-3              # R11
@@ -195,10 +195,10 @@ def transforms(theta, K):
 
 
 def tissue_signal(s0, frac, d, fin, bvals, bvecs):
-    """Sec. 2.2 Eq. 2: S = S0 (f_csf E_csf + f_gm E_gm + sum_k f_wm,k E_wm,k + f_res E_res)."""
+    """Sec. 2.2 Eq. 3: S = S0 (f_csf E_csf + f_gm E_gm + sum_k f_wm,k E_wm,k + f_res E_res)."""
     K = d.shape[1]
     b = bvals[None, :]
-    e_csf = torch.exp(-b * D_CSF)                     # Eq. 3
+    e_csf = torch.exp(-b * D_CSF)                     # Eq. 4
     e_gm = torch.exp(-b * D_GM)
     e_res = torch.exp(-b * D_RES)
     cos = torch.einsum("vkj,nj->vkn", d, bvecs)        # cos(theta) = d_k . g_n
@@ -207,7 +207,7 @@ def tissue_signal(s0, frac, d, fin, bvals, bvecs):
     bb = bvals[None, None, :]
     f_in = fin[:, None, None]
     e_wm = (f_in * torch.exp(-bb * D_PAR * cos2)
-            + (1.0 - f_in) * torch.exp(-bb * (D_PAR * cos2 + D_PERP * sin2)))   # Eq. 4
+            + (1.0 - f_in) * torch.exp(-bb * (D_PAR * cos2 + D_PERP * sin2)))   # Eq. 5
     mix = frac[:, 0:1] * e_csf + frac[:, 1:2] * e_gm + frac[:, K + 2:K + 3] * e_res
     mix = mix + (frac[:, 2:K + 2, None] * e_wm).sum(1)
     return s0[:, None] * mix
@@ -267,7 +267,7 @@ def group_init(ov):
 
 
 def predict(ov, theta, gp):
-    """Calibrated prediction y_hat [V, N] (Sec. 2.3 Eq. 5) and the tissue signal S."""
+    """Calibrated prediction y_hat [V, N] (Sec. 2.3 Eq. 6) and the tissue signal S."""
     K = ov.opts.K
     s0, frac, d, fin = transforms(theta, K)
     S = tissue_signal(s0, frac, d, fin, ov.bvals, ov.bvecs)
@@ -290,12 +290,12 @@ def objective(ov, theta, gp, n_norm=None):
     y = ov.y
     parts = {}
     if o.loss == "mse":
-        parts["data"] = ((yhat - y) ** 2).sum() / M                        # Eq. 7
+        parts["data"] = ((yhat - y) ** 2).sum() / M                        # Eq. 8
     elif o.loss == "nll":
         sig2 = torch.exp(2.0 * gp["sigma_log"])
         z = y * yhat / sig2
         parts["data"] = (2.0 * gp["sigma_log"] + (y * y + yhat * yhat) / (2.0 * sig2)
-                         - log_i0(z)).sum()                                 # Eq. 8
+                         - log_i0(z)).sum()                                 # Eq. 9
     else:
         raise ValueError(o.loss)
     s0, frac, d, fin = transforms(theta, K)
@@ -318,7 +318,7 @@ def objective(ov, theta, gp, n_norm=None):
         fn = frac[safe] * valid[..., None]                                   # [V, 6, K+3]
         mean = fn.sum(1) / torch.clamp(cnt, min=1)[:, None]
         r = frac - mean
-        parts["spatial"] = o.lam_sp * (huber(r, o.huber_delta).sum(1) * has).sum() / M  # Eq. 6
+        parts["spatial"] = o.lam_sp * (huber(r, o.huber_delta).sum(1) * has).sum() / M  # Eq. 7
     if o.lam_dir:
         dn = d[safe]                                                         # [V, 6, K, 3]
         dot = (d[:, None] * dn).sum(-1)                                      # [V, 6, K]

@@ -1,5 +1,5 @@
 """Writes bessel_fit.h: float32 approximations of the modified Bessel functions
-that the Rician NLL (Eq. 8) and its gradient need.
+that the Rician NLL (Eq. 9) and its gradient need.
 
 For z < ZS the kernels sum the power series (A&S 9.6.10)
     I0(z) = sum_k t^k / (k!)^2,   I1(z) = (z/2) sum_k t^k / (k! (k+1)!),   t = z^2/4,

@@ -80,7 +80,7 @@ __global__ void k_table(const float* bvals, const float* bvecs, int N, MeasRow* 
   if (n >= N) return;
   const double b = bvals[n];
   const double L2E = 1.4426950408889634;
-  const double dpar = 1.7e-3, dperp = 0.4e-3;          // Eq. 4, mm^2/s
+  const double dpar = 1.7e-3, dperp = 0.4e-3;          // Eq. 5, mm^2/s
   MeasRow r;
   r.gx = bvecs[3 * n];
   r.gy = bvecs[3 * n + 1];
@@ -88,7 +88,7 @@ __global__ void k_table(const float* bvals, const float* bvecs, int N, MeasRow* 
   r.nkpar = static_cast<float>(-b * dpar * L2E);
   r.nkperp = static_cast<float>(-b * dperp * L2E);
   r.nkd = static_cast<float>(-b * (dpar - dperp) * L2E);
-  r.ecsf = static_cast<float>(exp(-b * 3.0e-3));          // Eq. 3
+  r.ecsf = static_cast<float>(exp(-b * 3.0e-3));          // Eq. 4
   r.egm = static_cast<float>(exp(-b * 0.9e-3));
   r.eres = static_cast<float>(exp(-b * 0.2e-3));
   r.An = static_cast<float>(-2.0 * b * dpar);

@@ -24,14 +24,14 @@ constexpr float kNormEps2 = 1e-24f;                  // |v| clamp 1e-12, squared
 enum : int { kStTimeout = 1, kStNonfinite = 2 };
 
 // One row of the per-measurement table (64 bytes, 16-byte aligned for the bulk copy).
-// With c = d_k . g_n and x = c^2 the fiber terms of Eq. 4 are
+// With c = d_k . g_n and x = c^2 the fiber terms of Eq. 5 are
 //   e1 = exp(-b D_par x) = 2^(nkpar x),
 //   p  = exp(-b (D_par x + D_perp (1 - x))) = 2^(nkperp + nkd x),
 //   E_wm = f_in e1 + (1 - f_in) p,   dE_wm/dc = c (An f_in e1 + Bn (1 - f_in) p).
 struct __align__(16) MeasRow {
   float gx, gy, gz, nkpar;       // g_n; -b D_par log2(e)
-  float nkperp, nkd, ecsf, egm;  // -b D_perp log2(e); -b (D_par - D_perp) log2(e); E_csf, E_gm (Eq. 3)
-  float eres, An, Bn, A;         // E_res; -2 b D_par; 2 b (D_perp - D_par); exp(alpha_n) (Eq. 5)
+  float nkperp, nkd, ecsf, egm;  // -b D_perp log2(e); -b (D_par - D_perp) log2(e); E_csf, E_gm (Eq. 4)
+  float eres, An, Bn, A;         // E_res; -2 b D_par; 2 b (D_perp - D_par); exp(alpha_n) (Eq. 6)
   float beta, pad0, pad1, pad2;  // beta_n
 };
 

@@ -1,8 +1,8 @@
 // Templated PRISM iteration kernels (K fibers, TPV threads per voxel, loss mode,
 // calibration on/off). Included by one translation unit per K.
 //
-// The forward model, data terms and priors follow the paper (Sec. 2.2 Eqs. 2-4,
-// Sec. 2.3 Eq. 5, Sec. 2.4, Sec. 2.5 Eqs. 7-8); the gradient is the hand-written
+// The forward model, data terms and priors follow the paper (Sec. 2.2 Eqs. 3-5,
+// Sec. 2.3 Eq. 6, Sec. 2.4, Sec. 2.5 Eqs. 8-9); the gradient is the hand-written
 // adjoint of those equations; the update is Adam (the paper's Table 2 comparator).
 #pragma once
 
@@ -248,7 +248,7 @@ __device__ __forceinline__ void acc_reduce_tpv(Acc<K>& A) {
   }
 }
 
-// One (voxel, measurement) pair: forward model (Eqs. 2-5), data-term derivative, and
+// One (voxel, measurement) pair: forward model (Eqs. 3-6), data-term derivative, and
 // accumulation of the adjoint. With EXT_R the caller supplies dL/dy_hat (plain
 // adjoint); rr_out returns dL/dy_hat (unscaled) and u_out the unscaled r A B S.
 // `ffin` / `fomf` are f_wm,k f_in and f_wm,k (1 - f_in).
@@ -581,20 +581,25 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_iter_fused(const IterArgs 
       tphase ^= 1;
       cur_group = tl.group;
     }
-    // L2 prefetch of the rows the epilogue reads (parameters, Adam moments, prior data)
+    // L2 prefetch of the per-voxel rows a tile reads (parameters, Adam moments, prior data):
+    // for the first tile now, and for the next tile one whole tile ahead of its use
     if (tid == 32) {
       const uint32_t rb = static_cast<uint32_t>(kFusedThreads / TPV) * 4u;
-      for (int q = 0; q < Q; ++q) {
-        const size_t o = static_cast<size_t>(q) * Vp + tl.slot0;
-        prefetch_l2(a.theta + o, rb);
-        prefetch_l2(a.m + o, rb);
-        prefetch_l2(a.v + o, rb);
-      }
-      if (a.nb_priors) {
-        for (int e = 0; e < 6; ++e) prefetch_l2(a.nbr + static_cast<size_t>(e) * Vp + tl.slot0, rb);
-        if (a.lam_sp > 0.f)
-          for (int c = 0; c < NF; ++c) prefetch_l2(a.hsp + static_cast<size_t>(c) * Vp + tl.slot0, rb);
-      }
+      auto rows = [&](int slot0) {
+        for (int q = 0; q < Q; ++q) {
+          const size_t o = static_cast<size_t>(q) * Vp + slot0;
+          prefetch_l2(a.theta + o, rb);
+          prefetch_l2(a.m + o, rb);
+          prefetch_l2(a.v + o, rb);
+        }
+        if (a.nb_priors) {
+          for (int e = 0; e < 6; ++e) prefetch_l2(a.nbr + static_cast<size_t>(e) * Vp + slot0, rb);
+          if (a.lam_sp > 0.f)
+            for (int c = 0; c < NF; ++c) prefetch_l2(a.hsp + static_cast<size_t>(c) * Vp + slot0, rb);
+        }
+      };
+      if (t == s_first) rows(tl.slot0);
+      if (t_next < a.ntiles) rows(t_next * (kFusedThreads / TPV));
     }
 
     const int slot = tl.slot0 + vl;
@@ -645,7 +650,7 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_iter_fused(const IterArgs 
         const float2* __restrict__ yc2 = reinterpret_cast<const float2*>(ring + s * (kChunk * VW)) + lv;
         const MeasPair* __restrict__ tab2 = reinterpret_cast<const MeasPair*>(s_tab) + j * (kChunk / 2);
         if (act && cnt == kChunk) {
-#pragma unroll
+#pragma unroll 2
           for (int i = 0; i < kChunk / 2; ++i) step2<K, false>(DP, tab2[i], yc2[i * VW], make_float2(1.f, 1.f), AP);
         } else if (act) {
           for (int i = 0; i < (cnt + 1) / 2; ++i)
@@ -944,7 +949,7 @@ __global__ void __launch_bounds__(256) k_adjoint(const IterArgs a, const PlainAr
   }
 }
 
-// Huber-Laplacian preparation: rho'(u_c(x)) / |N(x)| and the prior value per voxel (Eq. 6).
+// Huber-Laplacian preparation: rho'(u_c(x)) / |N(x)| and the prior value per voxel (Eq. 7).
 template <int K>
 __global__ void k_prior_prep(const IterArgs a, int tile_begin, int tile_end) {
   constexpr int NF = K + 3, XF = 4 * K + 3;

@@ -8,7 +8,7 @@
 // pass every input and output buffer; the only other memory used is the fixed
 // file-scope array below, which every GPU that loads the library holds until exit.
 //
-// It evaluates, for n_vox voxels of one group, the MSE data term (Eq. 7) with the
+// It evaluates, for n_vox voxels of one group, the MSE data term (Eq. 8) with the
 // repulsion and sparsity priors (no calibration, no neighbour priors), on raw signal
 // rows b0-normalised inline, exactly as prism_forward / prism_backward do for such a
 // problem, and writes J and dJ/dtheta. The paper has no counterpart of this entry point.

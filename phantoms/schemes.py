@@ -4,7 +4,7 @@ Directions on each shell minimise the antipodally symmetric Coulomb energy
     E = sum_{i<j} 1/|x_i - x_j| + 1/|x_i + x_j|
 over unit vectors (Jones et al. 1999 style), by projected gradient descent from
 a seeded random start. The schemes match the workloads the paper describes:
-3 shells at b = 1000/2000/3000 s/mm^2 (Sec. 4 "Datasets"), and the 96-, 288-
+3 shells at b = 1000/2000/3000 s/mm^2 (Sec. 3 "Datasets"), and the 96-, 288-
 and 360-measurement layouts of the synthetic benchmarks.
 """
 import numpy as np

@@ -1,4 +1,4 @@
-"""Seeded phantoms shaped like the paper's workloads (Sec. 4 "Datasets").
+"""Seeded phantoms shaped like the paper's workloads (Sec. 3 "Datasets").
 
 Generators return `Volume` objects (mask, masked signal rows, scheme, ground
 truth). The ground-truth simulator is a multi-compartment stick-and-zeppelin

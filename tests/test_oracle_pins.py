@@ -71,7 +71,7 @@ def _single_fiber_theta(V, K, vraw, u_in, s0=1.0):
 
 @pytest.mark.parametrize("K", [1, 3])
 def test_single_stick_closed_form(K):
-    """f_wm=1, f_intra=1, S0=1, no calibration => y_hat = exp(-b D_par cos^2) (Eq. 4)."""
+    """f_wm=1, f_intra=1, S0=1, no calibration => y_hat = exp(-b D_par cos^2) (Eq. 5)."""
     angles = [0.0, 30.0, 45.0, 60.0, 90.0]
     bv, gv = _line_scheme(1000.0, angles)
     mask = np.ones((1, 1, 1), np.uint8)
@@ -97,7 +97,7 @@ def test_zeppelin_only_closed_form():
 
 
 def test_isotropic_closed_form():
-    """All fraction in one isotropic pool gives exp(-b D) of that pool (Eq. 3)."""
+    """All fraction in one isotropic pool gives exp(-b D) of that pool (Eq. 4)."""
     bv, gv = _line_scheme(1500.0, [10.0])
     mask = np.ones((1, 1, 1), np.uint8)
     ov = _vol(mask, np.ones((1, 2), np.float32), bv, gv, K=2)
@@ -319,7 +319,7 @@ def test_sparsity_hand_value():
 
 
 def test_spatial_prior_hand_values():
-    """Eq. 6 on a 3-voxel line: constant fractions give 0; one bump gives the Huber value."""
+    """Eq. 7 on a 3-voxel line: constant fractions give 0; one bump gives the Huber value."""
     mask = np.ones((3, 1, 1), np.uint8)
     K = 1
     th = _frac_theta(3, K, [0.0], iso_logit=0.0, dirs=[[1, 0, 0]] * 3)
