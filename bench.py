@@ -294,7 +294,8 @@ def run_ours(args):
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{args.cpu_patches} fullest 16^3 patches ({nvox} voxels) x {args.cpu_iters} iterations, "
                          f"{dt:.1f} s"}
-    launches = (2 if PRIORS["lam_sp"] > 0 else 1) + 2
+    # per iteration: neighbour-prior preparation + fused kernel (groups finalised inside it)
+    launches = (2 if PRIORS["lam_sp"] > 0 else 1)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",

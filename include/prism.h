@@ -169,7 +169,9 @@ int prism_backward(prism_handle* h, float* grad_theta, float* grad_groups, void*
  * events on `stream` around each kernel class, waits for them, and writes the average
  * milliseconds per iteration to ms_out (HOST float[4]): [0] the fused iteration kernel,
  * [1] the neighbour-prior preparation kernel, [2] the group kernels (bias gradient,
- * reductions, group Adam), [3] the whole iteration. The iterations are real updates.
+ * reductions, group Adam; launched only with calibration -- otherwise the fused kernel's
+ * last CTA finalises the groups and [2] is 0), [3] the whole iteration. The iterations are
+ * real updates.
  * E_STATE on a handle created with fused = 0.
  */
 int prism_profile(prism_handle* h, int32_t n_iters, void* stream, float* ms_out);

@@ -390,7 +390,32 @@ class Adam:
 
 
 # ----------------------------------------------------------------------------
-# The fit: T iterations of (objective, gradient, Adam) over all volumes.
+# Rprop (Riedmiller & Braun 1993), the paper's solver (Sec. 2.5, Table 2): per-parameter
+# step sizes grow by eta_plus while the gradient keeps its sign, shrink by eta_minus
+# after a sign change (that step is skipped and the stored gradient is zeroed), clamped
+# to [step_min, step_max]; the update is -sign(g) * step. Initial step = lr.
+# ----------------------------------------------------------------------------
+class Rprop:
+    def __init__(self, opts, etas=(0.5, 1.2), step_sizes=(1e-6, 50.0)):
+        self.o = opts
+        self.eta_minus, self.eta_plus = etas
+        self.step_min, self.step_max = step_sizes
+        self.t = 0
+        self.state = {}
+
+    def step(self, name, p, g):
+        prev, size = self.state.get(name, (torch.zeros_like(p), torch.full_like(p, self.o.lr)))
+        sgn = torch.sign(g * prev)
+        size = torch.where(sgn > 0, torch.clamp(size * self.eta_plus, max=self.step_max),
+                           torch.where(sgn < 0, torch.clamp(size * self.eta_minus, min=self.step_min), size))
+        g = torch.where(sgn < 0, torch.zeros_like(g), g)
+        p = p - torch.sign(g) * size
+        self.state[name] = (g, size)
+        return p
+
+
+# ----------------------------------------------------------------------------
+# The fit: T iterations of (objective, gradient, Adam or Rprop) over all volumes.
 # ----------------------------------------------------------------------------
 @dataclass
 class FitResult:
@@ -400,11 +425,11 @@ class FitResult:
     parts_history: list = field(default_factory=list)
 
 
-def fit(vols, theta0, T, record_parts=False):
-    """Runs T Adam iterations; theta0 is a list of [V_g, Q] float64 tensors."""
+def fit(vols, theta0, T, record_parts=False, optimizer="adam"):
+    """Runs T iterations of Adam (default) or Rprop; theta0 is a list of [V_g, Q] float64 tensors."""
     thetas = [t.detach().clone().to(F64) for t in theta0]
     groups = [group_init(ov) for ov in vols]
-    adam = Adam(vols[0].opts)
+    adam = Adam(vols[0].opts) if optimizer == "adam" else Rprop(vols[0].opts)
     hist = np.zeros((T, len(vols)))
     parts_hist = []
     for it in range(T):

@@ -258,6 +258,14 @@ void fill_args(prism_handle* h) {
   a.beta2 = o.beta2;
   a.eps = o.eps;
   a.nb_priors = h->nb ? 1 : 0;
+  a.fold_groups = h->cal ? 0 : 1;
+  a.loss_mode = o.loss;
+  a.hist_len = kHistLen;
+  a.gparams_rw = h->d_gparams;
+  a.gm = h->d_gm;
+  a.gv = h->d_gv;
+  a.gloss = h->d_gloss;
+  a.hist = h->d_hist;
 
   GroupArgs& g = h->ga;
   g.G = h->G;
@@ -289,9 +297,11 @@ int enqueue_fused_iter(prism_handle* h, cudaStream_t st) {
   const IterArgs& a = h->ia;
   if (h->opt.lam_sp > 0.f) CK(h->ks->prior_prep(a, 0, h->ntiles, st));
   CK(h->ks->fused(a, h->opt.loss, h->cal ? 1 : 0, h->TPV, h->fused_grid, h->NT, h->fused_smem, st));
-  if (h->cal) CK(launch_bias_grad(a, h->ga, st));
-  CK(launch_group_reduce(a, h->ga, 1 | (h->cal ? 2 : 0), st));
-  CK(launch_group_adam(a, h->ga, 1 | 2, st));
+  if (h->cal) {   // without calibration the fused kernel's last CTA finalises the groups
+    CK(launch_bias_grad(a, h->ga, st));
+    CK(launch_group_reduce(a, h->ga, 1 | 2, st));
+    CK(launch_group_adam(a, h->ga, 1 | 2, st));
+  }
   return PRISM_OK;
 }
 
@@ -980,8 +990,8 @@ extern "C" int prism_profile(prism_handle* h, int32_t n_iters, void* stream, flo
       e = h->ks->fused(a, h->opt.loss, h->cal ? 1 : 0, h->TPV, h->fused_grid, h->NT, h->fused_smem, st);
     if (e == cudaSuccess) e = cudaEventRecord(ev[2], st);
     if (e == cudaSuccess && h->cal) e = launch_bias_grad(a, h->ga, st);
-    if (e == cudaSuccess) e = launch_group_reduce(a, h->ga, 1 | (h->cal ? 2 : 0), st);
-    if (e == cudaSuccess) e = launch_group_adam(a, h->ga, 1 | 2, st);
+    if (e == cudaSuccess && h->cal) e = launch_group_reduce(a, h->ga, 1 | 2, st);
+    if (e == cudaSuccess && h->cal) e = launch_group_adam(a, h->ga, 1 | 2, st);
     if (e == cudaSuccess) e = cudaEventRecord(ev[3], st);
     if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
     if (e != cudaSuccess) {

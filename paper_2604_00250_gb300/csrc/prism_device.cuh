@@ -95,6 +95,14 @@ struct IterArgs {
   float lam_rep, lam_sparse, tau, lam_sp, huber_delta, lam_dir, w_tv, tv_eps;
   float lr, beta1, beta2, eps;
   int32_t nb_priors;       // spatial or directional prior active
+  // Group finalisation done by the fused kernel's last CTA when no group has calibration:
+  // objective per group, its history, Adam on sigma_log (NLL), step counter.
+  int32_t fold_groups, loss_mode, hist_len, pad_;
+  float* gparams_rw;       // same array as gparams
+  float* gm;               // group Adam moments (packed like gparams)
+  float* gv;
+  double* gloss;           // [G]
+  double* hist;            // [hist_len][G]
 };
 
 // Packed signal layout: a tile's block holds TV / VW warp slices; slice w holds NP x VW
@@ -185,10 +193,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 // ---------------------------------------------------------------------------
 // Scalar helpers.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float softplusf_(float s) {   // log(1 + e^s), stable
-  return fmaxf(s, 0.f) + log1pf(expf(-fabsf(s)));
-}
-__device__ __forceinline__ float sigmoidf_(float s) { return 1.f / (1.f + expf(-s)); }
 
 // Huber rho and its derivative (transition delta).
 __device__ __forceinline__ float huber_rho(float r, float dl) {

@@ -29,35 +29,53 @@ __device__ __forceinline__ void load_theta(const float* __restrict__ theta, int 
   for (int q = 0; q < 4 * K + 5; ++q) th[q] = act ? theta[static_cast<size_t>(q) * Vp + slot] : 0.f;
 }
 
+// Per-voxel transforms (Sec. 2.2 "Per-voxel parameters", Sec. 2.5 constraints), evaluated with
+// special-function-unit approximations (2^x, log2, 1/x, 1/sqrt: relative error ~2^-22). Every
+// kernel uses this one definition, so the neighbour-prior inputs written by any kernel are
+// bitwise the ones the fused kernel would write.
+__device__ __forceinline__ float fexp(float x) { return ex2f_(x * kLog2e); }
+__device__ __forceinline__ float frcp(float x) { return rcpf_(x); }
+__device__ __forceinline__ float fsoftplus(float s) {   // max(s,0) + log1p(e^{-|s|})
+  const float e = fexp(-fabsf(s));
+  const float l = (e < 1e-3f) ? e * fmaf(-0.5f, e, 1.f) : lg2f_(1.f + e) * kLn2;
+  return fmaxf(s, 0.f) + l;
+}
+__device__ __forceinline__ float fsigmoid(float s) { return frcp(1.f + fexp(-s)); }
+
 template <int K>
 __device__ __forceinline__ void transform(const float (&th)[4 * K + 5], Vox<K>& P) {
   constexpr int NF = K + 3;
-  P.S0 = softplusf_(th[0]);
-  P.dS0 = sigmoidf_(th[0]);
+  P.S0 = fsoftplus(th[0]);
+  P.dS0 = fsigmoid(th[0]);
   float mx = th[1];
 #pragma unroll
   for (int i = 1; i < NF; ++i) mx = fmaxf(mx, th[1 + i]);
   float sum = 0.f;
 #pragma unroll
   for (int i = 0; i < NF; ++i) {
-    P.f[i] = expf(th[1 + i] - mx);
+    P.f[i] = fexp(th[1 + i] - mx);
     sum += P.f[i];
   }
-  const float isum = 1.f / sum;
+  const float isum = frcp(sum);
 #pragma unroll
   for (int i = 0; i < NF; ++i) P.f[i] *= isum;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const float vx = th[K + 4 + 3 * k], vy = th[K + 5 + 3 * k], vz = th[K + 6 + 3 * k];
-    const float n2 = fmaxf(vx * vx + vy * vy + vz * vz, kNormEps2);
-    const float in = rsqrtf(n2);
+    const float in = rsqrtf(fmaxf(vx * vx + vy * vy + vz * vz, kNormEps2));
     P.inrm[k] = in;
     P.d[k][0] = vx * in;
     P.d[k][1] = vy * in;
     P.d[k][2] = vz * in;
   }
-  P.fin = sigmoidf_(th[4 * K + 4]);
+  P.fin = fsigmoid(th[4 * K + 4]);
   P.omf = 1.f - P.fin;
+}
+
+__device__ __forceinline__ float fsqrt(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 
 // Gradient w.r.t. transformed parameters -> raw parameters (adjoint of `transform`).
@@ -491,6 +509,61 @@ constexpr int kChunk = 16;    // measurements per ring stage
 constexpr int kStages = 4;    // ring depth per warp
 constexpr int kFusedThreads = 128;
 
+// Last CTA of an uncalibrated fused iteration: fixed-order sums of the tiles' partials per
+// group (strided over threads, then a fixed tree), the objective and its history, Adam on
+// sigma_log for the Rician NLL, the step counter and the next iteration's Adam constants.
+__device__ __forceinline__ void finalize_groups(const IterArgs& a, double (*s_sum)[kFusedThreads]) {
+  const int tid = threadIdx.x;
+  const int step = *a.step;
+  bool bad = false;
+  for (int gi = 0; gi < a.G; ++gi) {
+    const GroupDev gr = a.groups[gi];
+    double l = 0.0, sg = 0.0, pr = 0.0;
+#pragma unroll 8
+    for (int t = gr.tile0 + tid; t < gr.tile0 + gr.ntiles; t += kFusedThreads) {
+      l += __ldcg(&a.tile_red[4 * static_cast<size_t>(t)]);
+      sg += __ldcg(&a.tile_red[4 * static_cast<size_t>(t) + 1]);
+      pr += __ldcg(&a.tile_red[4 * static_cast<size_t>(t) + 2]);
+    }
+    s_sum[0][tid] = l;
+    s_sum[1][tid] = sg;
+    s_sum[2][tid] = pr;
+    __syncthreads();
+    for (int o = kFusedThreads / 2; o > 0; o >>= 1) {
+      if (tid < o) {
+        s_sum[0][tid] += s_sum[0][tid + o];
+        s_sum[1][tid] += s_sum[1][tid + o];
+        s_sum[2][tid] += s_sum[2][tid + o];
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      const double J = s_sum[0][0] + s_sum[2][0];
+      a.gloss[gi] = J;
+      a.hist[static_cast<size_t>(step % a.hist_len) * a.G + gi] = J;
+      if (!isfinite(J)) bad = true;
+      if (a.loss_mode == kLossNLL) {
+        const int i = gr.gp_off;
+        const float gsig = static_cast<float>(s_sum[1][0]);
+        const float mq = fmaf(a.beta1, a.gm[i], (1.f - a.beta1) * gsig);
+        const float vq = fmaf(a.beta2, a.gv[i], (1.f - a.beta2) * gsig * gsig);
+        a.gm[i] = mq;
+        a.gv[i] = vq;
+        a.gparams_rw[i] -= a.adamc[0] * mq / fmaf(sqrtf(vq), a.adamc[1], a.eps);
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (bad) atomicOr(a.status, kStNonfinite);
+    *const_cast<int32_t*>(a.step) = step + 1;
+    const double t2 = static_cast<double>(step) + 2.0;
+    float* ac = const_cast<float*>(a.adamc);
+    ac[0] = static_cast<float>(a.lr / (1.0 - pow(static_cast<double>(a.beta1), t2)));
+    ac[1] = static_cast<float>(1.0 / sqrt(1.0 - pow(static_cast<double>(a.beta2), t2)));
+  }
+}
+
 template <int K, int TPV, int LOSS, bool CAL>
 __global__ void __launch_bounds__(kFusedThreads, 4) k_iter_fused(const IterArgs a) {
   constexpr int NF = K + 3, Q = 4 * K + 5, XF = 4 * K + 3;
@@ -731,7 +804,7 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_iter_fused(const IterArgs 
       float vq = writer ? a.v[ix] : 0.f;
       mq = fmaf(a.beta1, mq, (1.f - a.beta1) * gq[q]);
       vq = fmaf(a.beta2, vq, (1.f - a.beta2) * gq[q] * gq[q]);
-      th[q] -= stepsz * mq / fmaf(sqrtf(vq), isbc2, a.eps);
+      th[q] -= stepsz * mq * frcp(fmaf(fsqrt(vq), isbc2, a.eps));
       if (writer) {
         a.m[ix] = mq;
         a.v[ix] = vq;
@@ -763,10 +836,21 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_iter_fused(const IterArgs 
     // let copies still in flight land before the CTA's shared memory is released
     for (uint32_t p = g; p < iss; ++p) mbar_wait(&s_full[warp][p % kStages], (p / kStages) & 1);
   }
-  // The last CTA to leave resets the queue for the next iteration.
+  // The last CTA to leave resets the queue for the next iteration (and, without
+  // calibration, finalises the groups).
+  __shared__ int s_last;
   if (tid == 0) {
     __threadfence();
-    if (atomicAdd(a.done, 1) == static_cast<int>(gridDim.x) - 1) {
+    s_last = (atomicAdd(a.done, 1) == static_cast<int>(gridDim.x) - 1);
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    if (!CAL && a.fold_groups) {
+      __shared__ double s_sum[3][kFusedThreads];
+      finalize_groups(a, s_sum);
+    }
+    if (tid == 0) {
       *a.queue = 0;
       *a.done = 0;
       __threadfence();

@@ -470,3 +470,28 @@ def test_planted_mistakes_are_caught(monkeypatch):
     monkeypatch.setattr(O, "D_RES", 0.0)
     with pytest.raises(AssertionError):
         test_isotropic_closed_form()
+
+
+def test_rprop_matches_torch_optim():
+    """Rprop equals torch.optim.Rprop (float64) over steps with sign changes, and its first
+    step is -lr * sign(g)."""
+    rng = np.random.default_rng(12)
+    o = O.Options(lr=0.01)
+    p0 = torch.as_tensor(rng.normal(size=30))
+    ours = O.Rprop(o)
+    p = p0.clone()
+    ref = p0.clone().requires_grad_(True)
+    opt = torch.optim.Rprop([ref], lr=o.lr, etas=(0.5, 1.2), step_sizes=(1e-6, 50.0))
+    signs = rng.choice([-1.0, 1.0], size=(8, 30))
+    signs[:, :5] = 1.0                     # these keep their sign: steps grow by 1.2 each time
+    for it in range(8):
+        g = torch.as_tensor(signs[it] * rng.uniform(0.1, 2.0, 30))
+        p_new = ours.step("p", p, g)
+        if it == 0:
+            np.testing.assert_allclose((p - p_new).numpy(), (o.lr * torch.sign(g)).numpy(), rtol=0, atol=1e-15)
+        p = p_new
+        opt.zero_grad()
+        ref.grad = g.clone()
+        opt.step()
+        np.testing.assert_allclose(p.numpy(), ref.detach().numpy(), rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(ours.state["p"][1][:5].numpy(), o.lr * 1.2 ** 7, rtol=1e-13)
