@@ -797,17 +797,27 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_iter_fused(const IterArgs 
     float gq[Q];
     chain_raw<K>(P, gS0, gf, gd, gfin, gq);
     const bool writer = act && (js == 0);
+    // Adam: every moment load is issued before any store (the stores could alias the loads
+    // as far as the compiler knows, which would serialise one memory round trip per parameter)
+    float mq[Q], vq[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       const size_t ix = static_cast<size_t>(q) * Vp + slot;
-      float mq = writer ? a.m[ix] : 0.f;
-      float vq = writer ? a.v[ix] : 0.f;
-      mq = fmaf(a.beta1, mq, (1.f - a.beta1) * gq[q]);
-      vq = fmaf(a.beta2, vq, (1.f - a.beta2) * gq[q] * gq[q]);
-      th[q] -= stepsz * mq * frcp(fmaf(fsqrt(vq), isbc2, a.eps));
-      if (writer) {
-        a.m[ix] = mq;
-        a.v[ix] = vq;
+      mq[q] = writer ? a.m[ix] : 0.f;
+      vq[q] = writer ? a.v[ix] : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      mq[q] = fmaf(a.beta1, mq[q], (1.f - a.beta1) * gq[q]);
+      vq[q] = fmaf(a.beta2, vq[q], (1.f - a.beta2) * gq[q] * gq[q]);
+      th[q] -= stepsz * mq[q] * frcp(fmaf(fsqrt(vq[q]), isbc2, a.eps));
+    }
+    if (writer) {
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const size_t ix = static_cast<size_t>(q) * Vp + slot;
+        a.m[ix] = mq[q];
+        a.v[ix] = vq[q];
         a.theta[ix] = th[q];
       }
     }
