@@ -58,6 +58,7 @@ typedef enum prism_status {
 
 enum { PRISM_LOSS_MSE = 0, PRISM_LOSS_NLL = 1 };
 enum { PRISM_MEM_HOST = 0, PRISM_MEM_DEVICE = 1 };
+enum { PRISM_OPT_ADAM = 0, PRISM_OPT_RPROP = 1 };
 enum { PRISM_MAX_K = 5, PRISM_BIAS_GRID = 8 };
 
 /* One volume = one calibration / noise group (Sec. 2.3: b_lr, alpha_n, beta_n, sigma). */
@@ -86,7 +87,11 @@ typedef struct prism_options {
   float lam_dir;          /* directional continuity, 0 = off (paper 0.005) */
   float w_alpha, w_beta, w_blr, w_tv, tv_eps; /* calibration regularisers: 1e-3 each, eps 1e-6 */
   float sigma_init;       /* sigma start when a volume has < 2 b=0 measurements, 0.05 */
-  float lr, beta1, beta2, eps; /* Adam: 1e-2, 0.9, 0.999, 1e-8 */
+  float lr, beta1, beta2, eps; /* Adam: 1e-2, 0.9, 0.999, 1e-8; lr is also Rprop's initial step */
+  int32_t optimizer;      /* PRISM_OPT_ADAM (default) or PRISM_OPT_RPROP, the paper's solver (Sec. 2.5) */
+  float rprop_eta_minus;  /* Rprop step factor after a gradient sign change, 0.5 */
+  float rprop_eta_plus;   /* Rprop step factor while the sign holds, 1.2 */
+  float rprop_step_min, rprop_step_max; /* Rprop step bounds, 1e-6 and 50 */
   int32_t fused;          /* 1: persistent fused iteration kernel; 0: plain unfused per-patch launches */
   int32_t use_graph;      /* 1: replay the fused iteration from a CUDA graph */
   int32_t threads_per_voxel; /* 1, 4 or 16 (measurements split across lanes); 0 = automatic */

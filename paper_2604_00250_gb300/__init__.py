@@ -32,13 +32,16 @@ def _torch():
 
 
 def options(**kw):
-    """prism_options with the paper's defaults, overridden by keyword (loss="mse"|"nll")."""
+    """prism_options with the paper's defaults, overridden by keyword (loss="mse"|"nll",
+    optimizer="adam"|"rprop")."""
     lib = _lib.load()
     o = _lib.Options()
     lib.prism_default_options(ctypes.byref(o))
     for k, v in kw.items():
         if k == "loss" and isinstance(v, str):
             v = {"mse": LOSS_MSE, "nll": LOSS_NLL}[v.lower()]
+        if k == "optimizer" and isinstance(v, str):
+            v = {"adam": _lib.OPT_ADAM, "rprop": _lib.OPT_RPROP}[v.lower()]
         if isinstance(v, bool):
             v = int(v)
         if not hasattr(o, k):

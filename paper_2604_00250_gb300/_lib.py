@@ -10,6 +10,7 @@ STATUS_NAMES = {1: "E_INVALID_ARG", 2: "E_SHAPE", 3: "E_CUDA", 4: "E_OOM", 5: "E
                 6: "E_TIMEOUT", 7: "E_STATE"}
 MEM_HOST, MEM_DEVICE = 0, 1
 LOSS_MSE, LOSS_NLL = 0, 1
+OPT_ADAM, OPT_RPROP = 0, 1
 
 EXPORTS = [
     "prism_default_options", "prism_fit_init", "prism_step", "prism_sync", "prism_info",
@@ -45,6 +46,8 @@ class Options(ctypes.Structure):
         ("w_tv", ctypes.c_float), ("tv_eps", ctypes.c_float), ("sigma_init", ctypes.c_float),
         ("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
         ("eps", ctypes.c_float),
+        ("optimizer", ctypes.c_int32), ("rprop_eta_minus", ctypes.c_float), ("rprop_eta_plus", ctypes.c_float),
+        ("rprop_step_min", ctypes.c_float), ("rprop_step_max", ctypes.c_float),
         ("fused", ctypes.c_int32), ("use_graph", ctypes.c_int32),
         ("threads_per_voxel", ctypes.c_int32), ("cta_threads", ctypes.c_int32),
         ("autotune", ctypes.c_int32), ("seed", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4),

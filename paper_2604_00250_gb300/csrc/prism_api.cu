@@ -150,6 +150,11 @@ extern "C" void prism_default_options(prism_options* o) {
   o->beta1 = 0.9f;
   o->beta2 = 0.999f;
   o->eps = 1e-8f;
+  o->optimizer = PRISM_OPT_ADAM;
+  o->rprop_eta_minus = 0.5f;
+  o->rprop_eta_plus = 1.2f;
+  o->rprop_step_min = 1e-6f;
+  o->rprop_step_max = 50.f;
   o->fused = 1;
   o->use_graph = 1;
   o->threads_per_voxel = 0;
@@ -182,6 +187,12 @@ int validate_options(const prism_options& o) {
   if (!(o.beta1 >= 0.f && o.beta1 < 1.f) || !(o.beta2 >= 0.f && o.beta2 < 1.f))
     return fail(PRISM_E_INVALID_ARG, "Adam betas must be in [0, 1)");
   if (!(o.eps > 0.f)) return fail(PRISM_E_INVALID_ARG, "Adam eps must be > 0");
+  if (o.optimizer != PRISM_OPT_ADAM && o.optimizer != PRISM_OPT_RPROP)
+    return fail(PRISM_E_INVALID_ARG, "optimizer must be PRISM_OPT_ADAM or PRISM_OPT_RPROP");
+  if (o.optimizer == PRISM_OPT_RPROP &&
+      !(o.rprop_eta_minus > 0.f && o.rprop_eta_minus < 1.f && o.rprop_eta_plus > 1.f && o.rprop_step_min > 0.f &&
+        o.rprop_step_max >= o.rprop_step_min && o.lr >= o.rprop_step_min && o.lr <= o.rprop_step_max))
+    return fail(PRISM_E_INVALID_ARG, "Rprop needs 0 < eta_minus < 1 < eta_plus and 0 < step_min <= lr <= step_max");
   if (o.threads_per_voxel != 0 && o.threads_per_voxel != 1 && o.threads_per_voxel != 4 && o.threads_per_voxel != 16)
     return fail(PRISM_E_INVALID_ARG, "threads_per_voxel must be 0, 1, 4 or 16");
   if (o.cta_threads != 0 && o.cta_threads != 128 && o.cta_threads != 256)
@@ -257,6 +268,11 @@ void fill_args(prism_handle* h) {
   a.beta1 = o.beta1;
   a.beta2 = o.beta2;
   a.eps = o.eps;
+  a.optimizer = o.optimizer;
+  a.eta_minus = o.rprop_eta_minus;
+  a.eta_plus = o.rprop_eta_plus;
+  a.step_min = o.rprop_step_min;
+  a.step_max = o.rprop_step_max;
   a.nb_priors = h->nb ? 1 : 0;
   a.fold_groups = h->cal ? 0 : 1;
   a.loss_mode = o.loss;

@@ -194,11 +194,19 @@ __global__ void k_adam_voxel(const IterArgs a, const PlainArgs pa) {
   for (int q = 0; q < a.Q; ++q) {
     const size_t ix = static_cast<size_t>(q) * a.Vpad + slot;
     const float g = pa.grad[ix];
-    const float mq = fmaf(a.beta1, a.m[ix], (1.f - a.beta1) * g);
-    const float vq = fmaf(a.beta2, a.v[ix], (1.f - a.beta2) * g * g);
-    a.m[ix] = mq;
-    a.v[ix] = vq;
-    a.theta[ix] -= stepsz * mq / fmaf(sqrtf(vq), isbc2, a.eps);
+    if (a.optimizer == 0) {
+      const float mq = fmaf(a.beta1, a.m[ix], (1.f - a.beta1) * g);
+      const float vq = fmaf(a.beta2, a.v[ix], (1.f - a.beta2) * g * g);
+      a.m[ix] = mq;
+      a.v[ix] = vq;
+      a.theta[ix] -= stepsz * mq / fmaf(sqrtf(vq), isbc2, a.eps);
+    } else {
+      float th = a.theta[ix], mq = a.m[ix], vq = a.v[ix];
+      rprop_update(th, mq, vq, g, a.lr, a.eta_minus, a.eta_plus, a.step_min, a.step_max);
+      a.theta[ix] = th;
+      a.m[ix] = mq;
+      a.v[ix] = vq;
+    }
   }
 }
 
@@ -360,11 +368,18 @@ __global__ void __launch_bounds__(256) k_group_adam(const IterArgs a, const Grou
       }
       if (g.gexport && (mode & 4)) g.gexport[base + i] = grad;
       if ((mode & 2) && train) {
-        const float mq = fmaf(a.beta1, g.gm[base + i], (1.f - a.beta1) * grad);
-        const float vq = fmaf(a.beta2, g.gv[base + i], (1.f - a.beta2) * grad * grad);
+        float mq, vq, xn = x;
+        if (a.optimizer == 0) {
+          mq = fmaf(a.beta1, g.gm[base + i], (1.f - a.beta1) * grad);
+          vq = fmaf(a.beta2, g.gv[base + i], (1.f - a.beta2) * grad * grad);
+          xn = x - stepsz * mq / fmaf(sqrtf(vq), isbc2, a.eps);
+        } else {
+          mq = g.gm[base + i];
+          vq = g.gv[base + i];
+          rprop_update(xn, mq, vq, grad, a.lr, a.eta_minus, a.eta_plus, a.step_min, a.step_max);
+        }
         g.gm[base + i] = mq;
         g.gv[base + i] = vq;
-        const float xn = x - stepsz * mq / fmaf(sqrtf(vq), isbc2, a.eps);
         g.gparams[base + i] = xn;
         if (i >= 4 && i < 4 + 2 * N4) {
           const int n = (i < 4 + N4) ? i - 4 : i - 4 - N4;

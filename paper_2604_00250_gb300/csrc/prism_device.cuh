@@ -94,6 +94,8 @@ struct IterArgs {
   int32_t* status;         // device status word
   float lam_rep, lam_sparse, tau, lam_sp, huber_delta, lam_dir, w_tv, tv_eps;
   float lr, beta1, beta2, eps;
+  int32_t optimizer;       // 0 Adam, 1 Rprop (m = previous gradient, v = step size)
+  float eta_minus, eta_plus, step_min, step_max;
   int32_t nb_priors;       // spatial or directional prior active
   // Group finalisation done by the fused kernel's last CTA when no group has calibration:
   // objective per group, its history, Adam on sigma_log (NLL), step counter.
@@ -188,6 +190,29 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     if (done) return true;
   }
   return false;
+}
+
+// ---------------------------------------------------------------------------
+// Parameter update: Adam (Kingma & Ba; the Table 2 comparator) or Rprop (Riedmiller &
+// Braun 1993, the paper's solver): the step grows by eta_plus while the gradient keeps
+// its sign and shrinks by eta_minus after a change (that step is skipped and the stored
+// gradient zeroed), within [step_min, step_max]; the initial step is lr. Rprop keeps the
+// previous gradient in m and the step in v (v == 0: not started).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void rprop_update(float& th, float& m, float& v, float g, float lr, float eta_minus,
+                                             float eta_plus, float step_min, float step_max) {
+  float step = (v == 0.f) ? lr : v;
+  const float s = g * m;
+  if (s > 0.f) {
+    step = fminf(step * eta_plus, step_max);
+  } else if (s < 0.f) {
+    step = fmaxf(step * eta_minus, step_min);
+    g = 0.f;
+  }
+  if (g > 0.f) th -= step;
+  else if (g < 0.f) th += step;
+  m = g;
+  v = step;
 }
 
 // ---------------------------------------------------------------------------

@@ -545,11 +545,19 @@ __device__ __forceinline__ void finalize_groups(const IterArgs& a, double (*s_su
       if (a.loss_mode == kLossNLL) {
         const int i = gr.gp_off;
         const float gsig = static_cast<float>(s_sum[1][0]);
-        const float mq = fmaf(a.beta1, a.gm[i], (1.f - a.beta1) * gsig);
-        const float vq = fmaf(a.beta2, a.gv[i], (1.f - a.beta2) * gsig * gsig);
-        a.gm[i] = mq;
-        a.gv[i] = vq;
-        a.gparams_rw[i] -= a.adamc[0] * mq / fmaf(sqrtf(vq), a.adamc[1], a.eps);
+        if (a.optimizer == 0) {
+          const float mq = fmaf(a.beta1, a.gm[i], (1.f - a.beta1) * gsig);
+          const float vq = fmaf(a.beta2, a.gv[i], (1.f - a.beta2) * gsig * gsig);
+          a.gm[i] = mq;
+          a.gv[i] = vq;
+          a.gparams_rw[i] -= a.adamc[0] * mq / fmaf(sqrtf(vq), a.adamc[1], a.eps);
+        } else {
+          float th = a.gparams_rw[i], mq = a.gm[i], vq = a.gv[i];
+          rprop_update(th, mq, vq, gsig, a.lr, a.eta_minus, a.eta_plus, a.step_min, a.step_max);
+          a.gparams_rw[i] = th;
+          a.gm[i] = mq;
+          a.gv[i] = vq;
+        }
       }
     }
     __syncthreads();
@@ -806,11 +814,17 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_iter_fused(const IterArgs 
       mq[q] = writer ? a.m[ix] : 0.f;
       vq[q] = writer ? a.v[ix] : 0.f;
     }
+    if (a.optimizer == 0) {
 #pragma unroll
-    for (int q = 0; q < Q; ++q) {
-      mq[q] = fmaf(a.beta1, mq[q], (1.f - a.beta1) * gq[q]);
-      vq[q] = fmaf(a.beta2, vq[q], (1.f - a.beta2) * gq[q] * gq[q]);
-      th[q] -= stepsz * mq[q] * frcp(fmaf(fsqrt(vq[q]), isbc2, a.eps));
+      for (int q = 0; q < Q; ++q) {
+        mq[q] = fmaf(a.beta1, mq[q], (1.f - a.beta1) * gq[q]);
+        vq[q] = fmaf(a.beta2, vq[q], (1.f - a.beta2) * gq[q] * gq[q]);
+        th[q] -= stepsz * mq[q] * frcp(fmaf(fsqrt(vq[q]), isbc2, a.eps));
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < Q; ++q)
+        rprop_update(th[q], mq[q], vq[q], gq[q], a.lr, a.eta_minus, a.eta_plus, a.step_min, a.step_max);
     }
     if (writer) {
 #pragma unroll

@@ -178,3 +178,26 @@ def test_nonfinite_signal_is_rejected():
     with pytest.raises(prism.PrismError) as e:
         prism.Fitter([v], prism.options(K=2))
     assert e.value.code == 5
+
+
+@pytest.mark.parametrize("fused,tpv,loss,cal", [(1, 1, "mse", False), (1, 4, "nll", True), (1, 1, "nll", False),
+                                                (0, 4, "mse", True)])
+def test_rprop_steps_match_oracle(fused, tpv, loss, cal):
+    """Three Rprop iterations (the paper's solver, Sec. 2.5) of every parameter, group ones
+    included. Rprop moves each parameter by +-step whatever the gradient's size, so a
+    parameter whose gradient sign is decided by rounding may take the other branch; all
+    others agree to float32 rounding."""
+    vols = _problem(cal)
+    K = 3
+    inits = inits_for(vols, K, 6)
+    kw = dict(K=K, loss=loss, calibration=cal, patch_dim=4, lam_sp=0.01, lam_dir=0.005, fused=fused,
+              use_graph=fused, threads_per_voxel=tpv, optimizer="rprop")
+    f, ovs = make_pair(vols, inits, **kw)
+    f.step(3)
+    f.sync()
+    th = f.params_host()
+    res = O.fit(ovs, [torch.as_tensor(t).double() for t in inits], 3, optimizer="rprop")
+    np.testing.assert_allclose(f.loss_history(), res.loss_history, rtol=1e-4)
+    d = np.abs(th - np.concatenate([t.numpy() for t in res.theta]))
+    assert float(np.mean(d < 1e-5)) >= 0.99, float(np.mean(d < 1e-5))
+    f.close()
