@@ -85,6 +85,10 @@ typedef struct prism_options {
   float lam_sp;           /* Huber-Laplacian fraction smoothness (Eq. 7), 0 = off (paper default 0.01) */
   float huber_delta;      /* Huber transition, 0.05 */
   float lam_dir;          /* directional continuity, 0 = off (paper 0.005) */
+  float lam_orphan;       /* orphan-WM suppression lam * mean exp(-S0/s_orphan) sum_k f_wm,k, 0 = off (paper 0.01) */
+  float s_orphan;         /* S0 scale of orphan-WM suppression, 0.05 */
+  float lam_order;        /* fiber ordering lam * mean sum_k max(0, f_wm,k+1 - f_wm,k), 0 = off (paper 0.01) */
+  int32_t connectivity;   /* neighbourhood of the neighbour priors: 6 or 26 (Sec. 2.4) */
   float w_alpha, w_beta, w_blr, w_tv, tv_eps; /* calibration regularisers: 1e-3 each, eps 1e-6 */
   float sigma_init;       /* sigma start when a volume has < 2 b=0 measurements, 0.05 */
   float lr, beta1, beta2, eps; /* Adam: 1e-2, 0.9, 0.999, 1e-8; lr is also Rprop's initial step */

@@ -49,6 +49,12 @@ Readings (paper silent or ambiguous):
   R15 sparsity: lambda_sparse * mean_x sum_k f_wm,k [f_wm,k < tau].
   R16 directional continuity: lambda_dir * (1/|M|) sum_x (1/|N(x)|)
       sum_{x' in N(x)} sum_k (1 - (d_k(x) . d_k(x'))^2).
+  R25 orphan-WM suppression (Sec. 2.4, form unstated): lambda_orphan * mean_x
+      exp(-S0(x) / s_orphan) sum_k f_wm,k(x), s_orphan = 0.05 (negligible at S0 ~ 1).
+  R26 fiber ordering (Sec. 2.4, form unstated): lambda_order * mean_x
+      sum_{k<K} max(0, f_wm,k+1 - f_wm,k), a hinge toward descending fractions; its
+      derivative at the kink (equal fractions, e.g. the equal-logit start) is 0, as for R14.
+  R27 26-connectivity: the 26 voxels of the 3x3x3 cube, masked and in the same patch.
   R18 sigma init: pooled std of the b0-normalised b=0 repeats of the volume
       (clamped to >= 1e-3); sigma_init option when fewer than two b=0 volumes.
   R19 b=0 measurements: b <= 50 s/mm^2; b0 = their per-voxel mean.
@@ -68,6 +74,8 @@ D_PAR, D_PERP = 1.7e-3, 0.4e-3
 B0_MAX = 50.0          # R19
 NORM_EPS = 1e-12       # R7
 NBR6 = ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1))
+NBR26 = NBR6 + tuple((i, j, k) for i in (-1, 0, 1) for j in (-1, 0, 1) for k in (-1, 0, 1)
+                     if abs(i) + abs(j) + abs(k) > 1)
 
 
 @dataclass
@@ -81,6 +89,10 @@ class Options:
     lam_sp: float = 0.0                # Huber-Laplacian (Eq. 7), default 0.01 when on
     huber_delta: float = 0.05
     lam_dir: float = 0.0               # directional continuity, 0.005 when on
+    lam_orphan: float = 0.0            # R25, 0.01 when on
+    s_orphan: float = 0.05
+    lam_order: float = 0.0             # R26, 0.01 when on
+    connectivity: int = 6              # R13 / R27
     w_alpha: float = 1e-3              # R11
     w_beta: float = 1e-3
     w_blr: float = 1e-3
@@ -148,8 +160,9 @@ class OracleVolume:
         index[tuple(self.coords.T)] = np.arange(len(sel))
         pid_grid = -np.ones(self.shape, dtype=np.int64)
         pid_grid[tuple(coords_all.T)] = pid_all
-        nb = -np.ones((len(sel), 6), dtype=np.int64)
-        for a, off in enumerate(NBR6):
+        offs = NBR6 if opts.connectivity == 6 else NBR26
+        nb = -np.ones((len(sel), len(offs)), dtype=np.int64)
+        for a, off in enumerate(offs):
             c = self.coords + np.asarray(off)
             ok = np.all((c >= 0) & (c < np.asarray(self.shape)), axis=1)
             cc = c[ok]
@@ -309,19 +322,23 @@ def objective(ov, theta, gp, n_norm=None):
     if o.lam_sparse:
         gate = (fwm < o.tau).to(F64)
         parts["sparse"] = o.lam_sparse * (fwm * gate).sum() / M
+    if o.lam_orphan:
+        parts["orphan"] = o.lam_orphan * (torch.exp(-s0 / o.s_orphan) * fwm.sum(1)).sum() / M   # R25
+    if o.lam_order and K > 1:
+        parts["order"] = o.lam_order * torch.relu(fwm[:, 1:] - fwm[:, :-1]).sum() / M  # R26
     nbr = ov.nbr
     valid = nbr >= 0
     cnt = valid.sum(1)
     safe = torch.where(valid, nbr, torch.zeros_like(nbr))
     has = cnt > 0
     if o.lam_sp:
-        fn = frac[safe] * valid[..., None]                                   # [V, 6, K+3]
+        fn = frac[safe] * valid[..., None]                                   # [V, |N|, K+3]
         mean = fn.sum(1) / torch.clamp(cnt, min=1)[:, None]
         r = frac - mean
         parts["spatial"] = o.lam_sp * (huber(r, o.huber_delta).sum(1) * has).sum() / M  # Eq. 7
     if o.lam_dir:
-        dn = d[safe]                                                         # [V, 6, K, 3]
-        dot = (d[:, None] * dn).sum(-1)                                      # [V, 6, K]
+        dn = d[safe]                                                         # [V, |N|, K, 3]
+        dot = (d[:, None] * dn).sum(-1)                                      # [V, |N|, K]
         term = ((1.0 - dot * dot).sum(-1) * valid).sum(1) / torch.clamp(cnt, min=1)
         parts["dir"] = o.lam_dir * term.sum() / M
     if o.calibration:

@@ -42,6 +42,8 @@ class Options(ctypes.Structure):
         ("patch_dim", ctypes.c_int32),
         ("lam_rep", ctypes.c_float), ("lam_sparse", ctypes.c_float), ("tau", ctypes.c_float),
         ("lam_sp", ctypes.c_float), ("huber_delta", ctypes.c_float), ("lam_dir", ctypes.c_float),
+        ("lam_orphan", ctypes.c_float), ("s_orphan", ctypes.c_float), ("lam_order", ctypes.c_float),
+        ("connectivity", ctypes.c_int32),
         ("w_alpha", ctypes.c_float), ("w_beta", ctypes.c_float), ("w_blr", ctypes.c_float),
         ("w_tv", ctypes.c_float), ("tv_eps", ctypes.c_float), ("sigma_init", ctypes.c_float),
         ("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),

@@ -143,6 +143,10 @@ extern "C" void prism_default_options(prism_options* o) {
   o->lam_sp = 0.f;
   o->huber_delta = 0.05f;
   o->lam_dir = 0.f;
+  o->lam_orphan = 0.f;
+  o->s_orphan = 0.05f;
+  o->lam_order = 0.f;
+  o->connectivity = 6;
   o->w_alpha = o->w_beta = o->w_blr = o->w_tv = 1e-3f;
   o->tv_eps = 1e-6f;
   o->sigma_init = 0.05f;
@@ -177,11 +181,14 @@ int validate_options(const prism_options& o) {
   if (o.loss != PRISM_LOSS_MSE && o.loss != PRISM_LOSS_NLL) return fail(PRISM_E_INVALID_ARG, "loss must be MSE (0) or NLL (1)");
   if (o.calibration != 0 && o.calibration != 1) return fail(PRISM_E_INVALID_ARG, "calibration must be 0 or 1");
   if (o.patch_dim < 1 || o.patch_dim > 64) return fail(PRISM_E_INVALID_ARG, "patch_dim must be in 1..64");
-  const float nn[] = {o.lam_rep, o.lam_sparse, o.tau, o.lam_sp, o.lam_dir, o.w_alpha, o.w_beta, o.w_blr, o.w_tv};
+  const float nn[] = {o.lam_rep, o.lam_sparse, o.tau, o.lam_sp, o.lam_dir, o.w_alpha, o.w_beta, o.w_blr, o.w_tv,
+                      o.lam_orphan, o.lam_order};
   for (float x : nn)
     if (!finite_nonneg(x)) return fail(PRISM_E_INVALID_ARG, "prior weights and tau must be finite and >= 0");
   if (!(o.huber_delta > 0.f) || !std::isfinite(o.huber_delta)) return fail(PRISM_E_INVALID_ARG, "huber_delta must be > 0");
   if (!(o.tv_eps > 0.f)) return fail(PRISM_E_INVALID_ARG, "tv_eps must be > 0");
+  if (!(o.s_orphan > 0.f) || !std::isfinite(o.s_orphan)) return fail(PRISM_E_INVALID_ARG, "s_orphan must be > 0");
+  if (o.connectivity != 6 && o.connectivity != 26) return fail(PRISM_E_INVALID_ARG, "connectivity must be 6 or 26");
   if (!(o.sigma_init > 0.f) || !std::isfinite(o.sigma_init)) return fail(PRISM_E_INVALID_ARG, "sigma_init must be > 0");
   if (!(o.lr > 0.f) || !std::isfinite(o.lr)) return fail(PRISM_E_INVALID_ARG, "lr must be > 0");
   if (!(o.beta1 >= 0.f && o.beta1 < 1.f) || !(o.beta2 >= 0.f && o.beta2 < 1.f))
@@ -274,6 +281,10 @@ void fill_args(prism_handle* h) {
   a.step_min = o.rprop_step_min;
   a.step_max = o.rprop_step_max;
   a.nb_priors = h->nb ? 1 : 0;
+  a.n_nbr = o.connectivity;
+  a.lam_orphan = o.lam_orphan;
+  a.inv_s_orphan = 1.f / o.s_orphan;
+  a.lam_order = o.lam_order;
   a.fold_groups = h->cal ? 0 : 1;
   a.loss_mode = o.loss;
   a.hist_len = kHistLen;
@@ -479,8 +490,23 @@ int build_plan(prism_handle* h, const prism_volume* vols, int n_vols, Plan& pl) 
   pl.vox_of_slot.assign(Vp, -1);
   pl.vcoord.assign(Vp, 0);
   pl.vflag.assign(Vp, 0);
-  pl.nbr.assign(6 * static_cast<size_t>(Vp), -1);
-  const int off[6][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
+  const int nnb = h->opt.connectivity;
+  pl.nbr.assign(static_cast<size_t>(nnb) * Vp, -1);
+  // the six face neighbours first (their bits 0-5 also flag the bias TV pairs), then the
+  // edge and corner neighbours of the 3x3x3 cube for 26-connectivity
+  int off[26][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
+  {
+    int e = 6;
+    for (int i = -1; i <= 1; ++i)
+      for (int j = -1; j <= 1; ++j)
+        for (int k = -1; k <= 1; ++k)
+          if (std::abs(i) + std::abs(j) + std::abs(k) > 1) {
+            off[e][0] = i;
+            off[e][1] = j;
+            off[e][2] = k;
+            ++e;
+          }
+  }
   for (int g = 0; g < n_vols; ++g) {
     const prism_volume& v = vols[g];
     const GroupDev& gr = h->groups[g];
@@ -495,12 +521,12 @@ int build_plan(prism_handle* h, const prism_volume* vols, int n_vols, Plan& pl) 
           const int patch = h->tiles[slot / TV].patch;
           uint32_t fl = 0;
           int cnt = 0;
-          for (int e = 0; e < 6; ++e) {
+          for (int e = 0; e < nnb; ++e) {
             const int xx = x + off[e][0], yy = y + off[e][1], zz = z + off[e][2];
             if (xx < 0 || yy < 0 || zz < 0 || xx >= v.nx || yy >= v.ny || zz >= v.nz) continue;
             const int64_t gj = (static_cast<int64_t>(xx) * v.ny + yy) * v.nz + zz;
             if (vidx[g][gj] < 0) continue;
-            fl |= 1u << e;   // TV neighbour inside the mask (any patch)
+            if (e < 6) fl |= 1u << e;   // TV neighbour inside the mask (any patch)
             const int sj = pl.slot_of_grid[gr.grid_off + gj];
             if (h->tiles[sj / TV].patch == patch) {
               pl.nbr[static_cast<size_t>(e) * Vp + slot] = sj;
@@ -563,7 +589,7 @@ int init_impl(prism_handle* h, const prism_volume* vols, int n_vols, cudaStream_
   RC(h->alloc(&h->d_gU, Vp));
   RC(h->alloc(&h->d_tile_ab, h->ab_len));
   RC(h->alloc(&h->d_tile_red, 4 * static_cast<size_t>(h->ntiles)));
-  RC(h->alloc(&h->d_nbr, 6 * static_cast<size_t>(Vp)));
+  RC(h->alloc(&h->d_nbr, static_cast<size_t>(o.connectivity) * Vp));
   RC(h->alloc(&h->d_vcoord, Vp));
   RC(h->alloc(&h->d_vflag, Vp));
   RC(h->alloc(&h->d_table, h->tab_rows));

@@ -78,9 +78,9 @@ struct IterArgs {
   float* xf;               // [2][4K+3][Vpad] fractions and unit directions (ping-pong by step parity)
   float* hsp;              // [K+3][Vpad] rho'(u) / |N| of the Huber-Laplacian prior
   float* lp;               // [Vpad] Huber-Laplacian prior value per voxel
-  const int32_t* nbr;      // [6][Vpad] same-patch masked neighbour slots or -1
+  const int32_t* nbr;      // [n_nbr][Vpad] same-patch masked neighbour slots or -1
   const uint32_t* vcoord;  // [Vpad] x | y << 10 | z << 20
-  const uint32_t* vflag;   // [Vpad] bits 0-5 TV neighbours (+x,-x,+y,-y,+z,-z) masked; bits 8-11 |N(x)|
+  const uint32_t* vflag;   // [Vpad] bits 0-5 TV neighbours (+x,-x,+y,-y,+z,-z) masked; bits 8-12 |N(x)|
   const MeasRow* table;    // per-group measurement tables
   const MeasPair* table2;  // the same, paired (see MeasPair)
   const float* gparams;    // packed group parameters
@@ -97,6 +97,8 @@ struct IterArgs {
   int32_t optimizer;       // 0 Adam, 1 Rprop (m = previous gradient, v = step size)
   float eta_minus, eta_plus, step_min, step_max;
   int32_t nb_priors;       // spatial or directional prior active
+  int32_t n_nbr;           // 6 or 26
+  float lam_orphan, inv_s_orphan, lam_order;
   // Group finalisation done by the fused kernel's last CTA when no group has calibration:
   // objective per group, its history, Adam on sigma_log (NLL), step counter.
   int32_t fold_groups, loss_mode, hist_len, pad_;

@@ -109,12 +109,13 @@ __device__ __forceinline__ void store_xf(float* __restrict__ xf, int Vp, int slo
     for (int c = 0; c < 3; ++c) xf[static_cast<size_t>(K + 3 + 3 * k + c) * Vp + slot] = P.d[k][c];
 }
 
-// Priors of Sec. 2.4 at one voxel: value, and gradient added to gf / gd (transformed space).
-// Repulsion and sparsity are local; the Huber-Laplacian uses the precomputed rho'(u)/|N|
-// of the voxel and its neighbours; directional continuity reads neighbour directions.
+// Priors of Sec. 2.4 at one voxel: value, and gradient added to gS0 / gf / gd (transformed
+// space). Repulsion, sparsity, orphan-WM suppression and fiber ordering are local; the
+// Huber-Laplacian uses the precomputed rho'(u)/|N| of the voxel and its neighbours;
+// directional continuity reads neighbour directions.
 template <int K>
 __device__ __forceinline__ float priors(const IterArgs& a, const Vox<K>& P, int slot, float inv_M,
-                                        const float* __restrict__ xf_cur, float (&gf)[K + 3],
+                                        const float* __restrict__ xf_cur, float& gS0, float (&gf)[K + 3],
                                         float (&gd)[K][3]) {
   constexpr int NF = K + 3;
   const int Vp = a.Vpad;
@@ -148,34 +149,50 @@ __device__ __forceinline__ float priors(const IterArgs& a, const Vox<K>& P, int 
         gf[2 + k] += w;
       }
   }
-  if (a.nb_priors) {
-    const uint32_t fl = a.vflag[slot];
-    const int ncnt = (fl >> 8) & 15;
-    if (ncnt > 0) {
-      int nb[6];
+  if (a.lam_orphan > 0.f) {   // lam mean exp(-S0/s) sum_k f_wm,k
+    const float w = a.lam_orphan * inv_M;
+    const float e = ex2f_(-P.S0 * a.inv_s_orphan * kLog2e);
+    float sf = 0.f;
 #pragma unroll
-      for (int e = 0; e < 6; ++e) nb[e] = a.nbr[static_cast<size_t>(e) * Vp + slot];
+    for (int k = 0; k < K; ++k) {
+      sf += P.f[2 + k];
+      gf[2 + k] = fmaf(w, e, gf[2 + k]);
+    }
+    val = fmaf(w * e, sf, val);
+    gS0 = fmaf(-w * a.inv_s_orphan * e, sf, gS0);
+  }
+  if (a.lam_order > 0.f && K > 1) {   // lam mean sum_k max(0, f_k+1 - f_k)
+    const float w = a.lam_order * inv_M;
+#pragma unroll
+    for (int k = 0; k + 1 < K; ++k) {
+      const float dfk = P.f[3 + k] - P.f[2 + k];
+      if (dfk > 0.f) {
+        val = fmaf(w, dfk, val);
+        gf[3 + k] += w;
+        gf[2 + k] -= w;
+      }
+    }
+  }
+  if (a.nb_priors) {
+    const int ncnt = (a.vflag[slot] >> 8) & 31;
+    if (ncnt > 0) {
+      const float inv_n = 1.f / static_cast<float>(ncnt);
+      const float wsp = a.lam_sp * inv_M, wdir = a.lam_dir * inv_M;
+      float hs[NF];
       if (a.lam_sp > 0.f) {
-        const float w = a.lam_sp * inv_M;
         val += a.lp[slot];
 #pragma unroll
-        for (int c = 0; c < NF; ++c) {
-          const float* hc = a.hsp + static_cast<size_t>(c) * Vp;
-          float s = hc[slot] * static_cast<float>(ncnt);
-#pragma unroll
-          for (int e = 0; e < 6; ++e)
-            if (nb[e] >= 0) s -= hc[nb[e]];
-          gf[c] = fmaf(w, s, gf[c]);
-        }
+        for (int c = 0; c < NF; ++c) hs[c] = a.hsp[static_cast<size_t>(c) * Vp + slot] * static_cast<float>(ncnt);
       }
-      if (a.lam_dir > 0.f) {
-        const float w = a.lam_dir * inv_M;
-        const float inv_n = 1.f / static_cast<float>(ncnt);
+      for (int e = 0; e < a.n_nbr; ++e) {
+        const int x = a.nbr[static_cast<size_t>(e) * Vp + slot];
+        if (x < 0) continue;
+        if (a.lam_sp > 0.f) {
 #pragma unroll
-        for (int e = 0; e < 6; ++e) {
-          const int x = nb[e];
-          if (x < 0) continue;
-          const int nx_cnt = (a.vflag[x] >> 8) & 15;
+          for (int c = 0; c < NF; ++c) hs[c] -= a.hsp[static_cast<size_t>(c) * Vp + x];
+        }
+        if (a.lam_dir > 0.f) {
+          const int nx_cnt = (a.vflag[x] >> 8) & 31;
           const float wgt = inv_n + 1.f / static_cast<float>(nx_cnt);
 #pragma unroll
           for (int k = 0; k < K; ++k) {
@@ -183,12 +200,16 @@ __device__ __forceinline__ float priors(const IterArgs& a, const Vox<K>& P, int 
 #pragma unroll
             for (int q = 0; q < 3; ++q) dx[q] = xf_cur[static_cast<size_t>(K + 3 + 3 * k + q) * Vp + x];
             const float c = P.d[k][0] * dx[0] + P.d[k][1] * dx[1] + P.d[k][2] * dx[2];
-            val = fmaf(w * inv_n, 1.f - c * c, val);
-            const float s = -2.f * w * c * wgt;
+            val = fmaf(wdir * inv_n, 1.f - c * c, val);
+            const float sc = -2.f * wdir * c * wgt;
 #pragma unroll
-            for (int q = 0; q < 3; ++q) gd[k][q] = fmaf(s, dx[q], gd[k][q]);
+            for (int q = 0; q < 3; ++q) gd[k][q] = fmaf(sc, dx[q], gd[k][q]);
           }
         }
+      }
+      if (a.lam_sp > 0.f) {
+#pragma unroll
+        for (int c = 0; c < NF; ++c) gf[c] = fmaf(wsp, hs[c], gf[c]);
       }
     }
   }
@@ -674,7 +695,7 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_iter_fused(const IterArgs 
           prefetch_l2(a.v + o, rb);
         }
         if (a.nb_priors) {
-          for (int e = 0; e < 6; ++e) prefetch_l2(a.nbr + static_cast<size_t>(e) * Vp + slot0, rb);
+          for (int e = 0; e < a.n_nbr; ++e) prefetch_l2(a.nbr + static_cast<size_t>(e) * Vp + slot0, rb);
           if (a.lam_sp > 0.f)
             for (int c = 0; c < NF; ++c) prefetch_l2(a.hsp + static_cast<size_t>(c) * Vp + slot0, rb);
         }
@@ -793,7 +814,7 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_iter_fused(const IterArgs 
       dsig = 2.f * N - inv_s2 * (A.l1 + 2.f * A.l2);
     }
     // ---- priors
-    float ploss = priors<K>(a, P, slot, gr.inv_M, xf_cur, gf, gd);
+    float ploss = priors<K>(a, P, slot, gr.inv_M, xf_cur, gS0, gf, gd);
     float gUv = A.u * scale;
     if (CAL && a.w_tv > 0.f) {
       const uint32_t fl = act ? a.vflag[slot] : 0u;
@@ -1068,20 +1089,24 @@ __global__ void k_prior_prep(const IterArgs a, int tile_begin, int tile_end) {
   const GroupDev gr = a.groups[tl.group];
   const int Vp = a.Vpad;
   const float* xf = a.xf + static_cast<size_t>((*a.step) & 1) * XF * Vp;
-  const int ncnt = (a.vflag[slot] >> 8) & 15;
+  const int ncnt = (a.vflag[slot] >> 8) & 31;
   float val = 0.f;
   if (ncnt == 0) {
     for (int c = 0; c < NF; ++c) a.hsp[static_cast<size_t>(c) * Vp + slot] = 0.f;
   } else {
-    int nb[6];
-    for (int e = 0; e < 6; ++e) nb[e] = a.nbr[static_cast<size_t>(e) * Vp + slot];
+    float sum[NF];
+#pragma unroll
+    for (int c = 0; c < NF; ++c) sum[c] = 0.f;
+    for (int e = 0; e < a.n_nbr; ++e) {
+      const int x = a.nbr[static_cast<size_t>(e) * Vp + slot];
+      if (x < 0) continue;
+#pragma unroll
+      for (int c = 0; c < NF; ++c) sum[c] += xf[static_cast<size_t>(c) * Vp + x];
+    }
     const float inv_n = 1.f / static_cast<float>(ncnt);
+#pragma unroll
     for (int c = 0; c < NF; ++c) {
-      const float* fc = xf + static_cast<size_t>(c) * Vp;
-      float s = 0.f;
-      for (int e = 0; e < 6; ++e)
-        if (nb[e] >= 0) s += fc[nb[e]];
-      const float u = fc[slot] - s * inv_n;
+      const float u = xf[static_cast<size_t>(c) * Vp + slot] - sum[c] * inv_n;
       val += huber_rho(u, a.huber_delta);
       a.hsp[static_cast<size_t>(c) * Vp + slot] = huber_drho(u, a.huber_delta) * inv_n;
     }
@@ -1113,8 +1138,9 @@ __global__ void __launch_bounds__(256) k_prior(const IterArgs a, const PlainArgs
 #pragma unroll
   for (int k = 0; k < K; ++k) gd[k][0] = gd[k][1] = gd[k][2] = 0.f;
   float val = 0.f;
+  float gS0 = 0.f;
   if (act) {
-    val = priors<K>(a, P, slot, gr.inv_M, xf_cur, gf, gd);
+    val = priors<K>(a, P, slot, gr.inv_M, xf_cur, gS0, gf, gd);
     if (gr.calib && a.w_tv > 0.f) {
       int x, y, z;
       unpack_coord(a.vcoord[slot], x, y, z);
@@ -1126,7 +1152,7 @@ __global__ void __launch_bounds__(256) k_prior(const IterArgs a, const PlainArgs
     }
     if (pa.mode & 2) {
       float g[Q];
-      chain_raw<K>(P, 0.f, gf, gd, 0.f, g);
+      chain_raw<K>(P, gS0, gf, gd, 0.f, g);
 #pragma unroll
       for (int q = 0; q < Q; ++q) pa.grad[static_cast<size_t>(q) * a.Vpad + slot] += g[q];
     }

@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kNaThreads) k_grad_noalloc(const float* __rest
   pa.lam_sparse = lam_sparse;
   pa.tau = tau;
   pa.nb_priors = 0;
-  const float ploss = act ? priors<K>(pa, P, 0, inv_M, nullptr, gf, gd) : 0.f;
+  const float ploss = act ? priors<K>(pa, P, 0, inv_M, nullptr, gS0, gf, gd) : 0.f;
   float g[Q];
   chain_raw<K>(P, gS0, gf, gd, gfin, g);
   if (act) {

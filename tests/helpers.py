@@ -16,7 +16,7 @@ TOL_GRAD = 1e-4
 
 OPT_KEYS = ("K", "loss", "calibration", "lam_rep", "lam_sparse", "tau", "lam_sp", "huber_delta", "lam_dir",
             "w_alpha", "w_beta", "w_blr", "w_tv", "tv_eps", "patch_dim", "sigma_init", "lr", "beta1",
-            "beta2", "eps")
+            "beta2", "eps", "lam_orphan", "s_orphan", "lam_order", "connectivity")
 
 
 def gpu_volume(vol, init=None, device_signal=False):

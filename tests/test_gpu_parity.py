@@ -28,6 +28,9 @@ CASES = [
     ("nll", True, 2, 16, dict()),
     ("mse", False, 1, 1, dict()),
     ("mse", False, 5, 4, dict(lam_sp=0.01)),
+    # remaining stabilisers of Sec. 2.4 and the 26-neighbourhood
+    ("mse", False, 3, 1, dict(lam_sp=0.01, lam_dir=0.005, lam_orphan=0.01, lam_order=0.01, connectivity=26)),
+    ("nll", True, 3, 4, dict(lam_sp=0.01, lam_orphan=0.01, s_orphan=0.5, lam_order=0.01, connectivity=26)),
 ]
 
 
@@ -200,4 +203,24 @@ def test_rprop_steps_match_oracle(fused, tpv, loss, cal):
     np.testing.assert_allclose(f.loss_history(), res.loss_history, rtol=1e-4)
     d = np.abs(th - np.concatenate([t.numpy() for t in res.theta]))
     assert float(np.mean(d < 1e-5)) >= 0.99, float(np.mean(d < 1e-5))
+    f.close()
+
+
+
+@pytest.mark.parametrize("tpv,loss,cal", [(1, "mse", False), (4, "nll", True)])
+def test_stabilisers_26_connectivity_steps(tpv, loss, cal):
+    """Three fused iterations with orphan-WM suppression, fiber ordering and 26-connected
+    neighbour priors against the oracle's trajectory."""
+    vols = _problem(cal)
+    K = 3
+    inits = inits_for(vols, K, 13)
+    kw = dict(K=K, loss=loss, calibration=cal, patch_dim=4, lam_sp=0.01, lam_dir=0.005, lam_orphan=0.01,
+              s_orphan=0.5, lam_order=0.01, connectivity=26, threads_per_voxel=tpv)
+    f, ovs = make_pair(vols, inits, **kw)
+    f.step(3)
+    f.sync()
+    res = O.fit(ovs, [torch.as_tensor(t).double() for t in inits], 3)
+    np.testing.assert_allclose(f.loss_history(), res.loss_history, rtol=1e-5)
+    th = f.params_host()
+    assert float(np.max(np.abs(th - np.concatenate([t.numpy() for t in res.theta])))) < 3e-4
     f.close()

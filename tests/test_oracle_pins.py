@@ -429,13 +429,14 @@ def test_gradient_central_differences(loss, cal, K):
     bv, gv = P.make_scheme(2, [(1000, 5), (2500, 5)], 8)
     vol = P.random_volume((2, 2, 2), scheme=(bv, gv), seed=8, calibration=cal)
     kw = dict(K=K, loss=loss, calibration=cal, lam_sp=0.01, lam_dir=0.005, patch_dim=2,
-              tau=0.15)
+              tau=0.15, lam_orphan=0.01, lam_order=0.01, connectivity=26 if cal else 6)
     ov = _vol(vol.mask, vol.signal, vol.bvals, vol.bvecs, **kw)
     # keep every WM fraction away from the sparsity gate (a jump) by >> h
     while True:
         th = torch.as_tensor(rng.normal(0, 0.7, size=(ov.n_vox, O.n_params(K))))
         _, fr, _, _ = O.transforms(th, K)
-        if float((fr[:, 2:K + 2] - 0.15).abs().min()) > 1e-3:
+        fw = fr[:, 2:K + 2]
+        if float((fw - 0.15).abs().min()) > 1e-3 and (K < 2 or float((fw[:, 1:] - fw[:, :-1]).abs().min()) > 1e-3):
             break
     gp = O.group_init(ov)
     gp["sigma_log"] = torch.tensor(math.log(0.06), dtype=F64)
@@ -495,3 +496,45 @@ def test_rprop_matches_torch_optim():
         opt.step()
         np.testing.assert_allclose(p.numpy(), ref.detach().numpy(), rtol=1e-13, atol=1e-15)
     np.testing.assert_allclose(ours.state["p"][1][:5].numpy(), o.lr * 1.2 ** 7, rtol=1e-13)
+
+
+def test_orphan_and_ordering_hand_values():
+    """R25: exp(-S0 / 0.05) sum_k f_wm (S0 = 0.05 -> e^-1); R26: hinge on ascending fractions."""
+    mask = np.ones((1, 1, 1), np.uint8)
+    K = 3
+    # wm fractions 0.2, 0.5, 0.3 (iso pools ~0): ordering violations 0.5-0.2 = 0.3
+    lg = [math.log(0.2), math.log(0.5), math.log(0.3)]
+    th = _frac_theta(1, K, lg, dirs=[[[1, 0, 0], [0, 1, 0], [0, 0, 1]]])
+    th[:, 0] = math.log(math.expm1(0.05))          # S0 = 0.05
+    parts = _prior_parts(mask, th, K, lam_rep=0, lam_sparse=0, lam_orphan=0.01, lam_order=0.01)
+    assert abs(float(parts["orphan"]) - 0.01 * math.exp(-1.0) * 1.0) < 1e-14
+    assert abs(float(parts["order"]) - 0.01 * 0.3) < 1e-14
+    # descending fractions: no ordering cost
+    th2 = _frac_theta(1, K, [math.log(0.5), math.log(0.3), math.log(0.2)], dirs=[[[1, 0, 0], [0, 1, 0], [0, 0, 1]]])
+    assert float(_prior_parts(mask, th2, K, lam_rep=0, lam_sparse=0, lam_order=0.01)["order"]) == 0.0
+
+
+def test_26_connectivity_neighbours():
+    """The 3x3x3 cube: an interior voxel has 26 neighbours, a corner 7; patches still bound them."""
+    mask = np.ones((3, 3, 3), np.uint8)
+    bv, gv = _line_scheme(1000.0, [0.0])
+    ov = _vol(mask, np.ones((27, 2), np.float32), bv, gv, K=1, connectivity=26, patch_dim=4)
+    cnt = (ov.nbr >= 0).sum(1).numpy()
+    # 8 corners x 7 + 12 edges x 11 + 6 faces x 17 + centre 26
+    assert cnt[13] == 26 and cnt[0] == 7 and cnt.sum() == 8 * 7 + 12 * 11 + 6 * 17 + 26
+    ov6 = _vol(mask, np.ones((27, 2), np.float32), bv, gv, K=1, connectivity=6, patch_dim=4)
+    assert (ov6.nbr >= 0).sum(1).numpy()[13] == 6
+    ov_split = _vol(mask, np.ones((27, 2), np.float32), bv, gv, K=1, connectivity=26, patch_dim=2)
+    c2 = (ov_split.nbr >= 0).sum(1).numpy()
+    assert c2[0] == 7 and c2[13] == 7 and c2[26] == 0      # (2,2,2) is alone in its 2^3 patch
+
+
+def test_ordering_kink_has_zero_derivative():
+    """R26 at equal fractions (the equal-logit start): value 0 and no gradient from the hinge."""
+    mask = np.ones((1, 1, 1), np.uint8)
+    bv, gv = _line_scheme(1000.0, [0.0])
+    ov = _vol(mask, np.ones((1, 2), np.float32), bv, gv, K=3, lam_rep=0, lam_sparse=0, lam_order=0.01)
+    th = _frac_theta(1, 3, [0.0, 0.0, 0.0], dirs=[[[1, 0, 0], [0, 1, 0], [0, 0, 1]]]).requires_grad_(True)
+    _, parts = O.objective(ov, th, O.group_init(ov))
+    (g,) = torch.autograd.grad(parts["order"], th)
+    assert float(parts["order"]) == 0.0 and float(g.abs().max()) == 0.0
