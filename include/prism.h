@@ -136,6 +136,16 @@ int prism_get_params(prism_handle* h, float* out, int32_t mem, void* stream);
 int prism_set_params(prism_handle* h, const float* in, int32_t mem, void* stream);
 
 /*
+ * Readout of the fitted fibers (Sec. 3 "Configuration": fiber directions are used directly
+ * as peaks): unit directions dirs [V][K][3], fractions fracs [V][K+3] ([csf, gm, wm_1..wm_K,
+ * res]) and peak flags peaks [V][K] (1 when the fiber's share of the white-matter fraction
+ * is >= rel_thresh, e.g. 0.15), mask order, in `mem` memory. Any output may be NULL.
+ * E_INVALID_ARG for rel_thresh outside [0, 1].
+ */
+int prism_get_fibers(prism_handle* h, float* dirs, float* fracs, uint8_t* peaks, float rel_thresh,
+                     int32_t mem, void* stream);
+
+/*
  * Packed group parameters. Group g occupies [off[4g], off[4g+4]) of the packed
  * float array: sigma_log at off[4g], alpha[N_g] at off[4g+1], beta[N_g] at
  * off[4g+2], b_lr[8][8][8] (C order) at off[4g+3]; off[4G] = total. `off` is a

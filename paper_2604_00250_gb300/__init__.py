@@ -190,6 +190,15 @@ class Fitter:
                                               _stream_ptr(stream)))
         torch.cuda.current_stream().synchronize()
 
+    def fibers(self, rel_thresh=0.15):
+        """(unit directions [V, K, 3], fractions [V, K+3], peak flags [V, K]) as numpy arrays."""
+        d = np.empty((self.n_vox, self.K, 3), dtype=np.float32)
+        f = np.empty((self.n_vox, self.K + 3), dtype=np.float32)
+        p = np.empty((self.n_vox, self.K), dtype=np.uint8)
+        _lib.check(self._lib.prism_get_fibers(self._h, d.ctypes.data, f.ctypes.data, p.ctypes.data,
+                                              float(rel_thresh), MEM_HOST, _stream_ptr(None)))
+        return d, f, p.astype(bool)
+
     def group_layout(self):
         off = np.zeros(4 * self.n_groups + 1, dtype=np.int64)
         _lib.check(self._lib.prism_group_layout(self._h, off.ctypes.data))

@@ -17,7 +17,7 @@ EXPORTS = [
     "prism_get_params", "prism_set_params", "prism_group_layout", "prism_get_groups",
     "prism_set_groups", "prism_get_loss", "prism_forward", "prism_backward", "prism_state_size",
     "prism_get_state", "prism_set_state", "prism_fit", "prism_fit_destroy", "prism_last_error",
-    "prism_profile", "prism_grad_noalloc", "prism_microbench",
+    "prism_profile", "prism_grad_noalloc", "prism_microbench", "prism_get_fibers",
 ]
 
 
@@ -92,6 +92,7 @@ def load():
         "prism_last_error": (ctypes.c_char_p, []),
         "prism_profile": (ctypes.c_int, [vp, i32, vp, vp]),
         "prism_microbench": (ctypes.c_int, [i32, vp, vp]),
+        "prism_get_fibers": (ctypes.c_int, [vp, vp, vp, vp, ctypes.c_float, i32, vp]),
         "prism_grad_noalloc": (ctypes.c_int, [vp, vp, vp, vp, i64, i32, i32, ctypes.c_float, ctypes.c_float,
                                               ctypes.c_float, vp, vp, vp]),
     }

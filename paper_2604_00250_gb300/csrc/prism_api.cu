@@ -922,6 +922,35 @@ extern "C" int prism_set_params(prism_handle* h, const float* in, int32_t mem, v
   return PRISM_OK;
 }
 
+extern "C" int prism_get_fibers(prism_handle* h, float* dirs, float* fracs, uint8_t* peaks, float rel_thresh,
+                                int32_t mem, void* stream) {
+  if (!h) return fail(PRISM_E_INVALID_ARG, "handle is NULL");
+  if (!(rel_thresh >= 0.f && rel_thresh <= 1.f)) return fail(PRISM_E_INVALID_ARG, "rel_thresh must be in [0, 1]");
+  if (mem != PRISM_MEM_HOST && mem != PRISM_MEM_DEVICE) return fail(PRISM_E_INVALID_ARG, "mem must be HOST or DEVICE");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int K = h->K;
+  const size_t nd = static_cast<size_t>(h->V) * K * 3, nf = static_cast<size_t>(h->V) * (K + 3),
+               np = static_cast<size_t>(h->V) * K;
+  if (mem == PRISM_MEM_DEVICE) {
+    CK(h->ks->fibers(h->ia, h->d_slot_of_vox, h->V, rel_thresh, dirs, fracs, peaks, st));
+    return PRISM_OK;
+  }
+  char* tmp = nullptr;
+  const size_t bytes = (dirs ? nd * 4 : 0) + (fracs ? nf * 4 : 0) + (peaks ? np : 0);
+  CK(cudaMalloc(&tmp, bytes > 0 ? bytes : 1));
+  float* dd = dirs ? reinterpret_cast<float*>(tmp) : nullptr;
+  float* df = fracs ? reinterpret_cast<float*>(tmp + (dirs ? nd * 4 : 0)) : nullptr;
+  uint8_t* dp = peaks ? reinterpret_cast<uint8_t*>(tmp + (dirs ? nd * 4 : 0) + (fracs ? nf * 4 : 0)) : nullptr;
+  cudaError_t e = h->ks->fibers(h->ia, h->d_slot_of_vox, h->V, rel_thresh, dd, df, dp, st);
+  if (e == cudaSuccess && dirs) e = cudaMemcpyAsync(dirs, dd, nd * 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && fracs) e = cudaMemcpyAsync(fracs, df, nf * 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && peaks) e = cudaMemcpyAsync(peaks, dp, np, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(tmp);
+  if (e != cudaSuccess) return cuda_fail(e, "prism_get_fibers");
+  return PRISM_OK;
+}
+
 extern "C" int prism_group_layout(const prism_handle* h, int64_t* off) {
   if (!h || !off) return fail(PRISM_E_INVALID_ARG, "NULL argument");
   std::memcpy(off, h->gp_layout.data(), h->gp_layout.size() * sizeof(int64_t));

@@ -922,6 +922,35 @@ __global__ void k_transform(const IterArgs a, int tile_begin, int tile_end) {
   store_xf<K>(a.xf + static_cast<size_t>((*a.step) & 1) * XF * a.Vpad, a.Vpad, slot, P);
 }
 
+// Readout (Sec. 3 "Configuration": fiber directions are the peaks): unit directions,
+// fractions and peak flags (a fiber's share of the WM fraction >= rel_thresh), mask order.
+template <int K>
+__global__ void k_fibers(const IterArgs a, const int32_t* __restrict__ slot_of_vox, int64_t V, float rel_thresh,
+                         float* __restrict__ dirs, float* __restrict__ fracs, uint8_t* __restrict__ peaks) {
+  const int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  float th[4 * K + 5];
+  load_theta<K>(a.theta, a.Vpad, slot_of_vox[v], true, th);
+  Vox<K> P;
+  transform<K>(th, P);
+  float wm = 0.f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) wm += P.f[2 + k];
+  const float inv_wm = 1.f / fmaxf(wm, 1e-12f);
+  if (fracs) {
+#pragma unroll
+    for (int i = 0; i < K + 3; ++i) fracs[v * (K + 3) + i] = P.f[i];
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (dirs) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) dirs[(v * K + k) * 3 + c] = P.d[k][c];
+    }
+    if (peaks) peaks[v * K + k] = (P.f[2 + k] * inv_wm >= rel_thresh) ? 1 : 0;
+  }
+}
+
 // Synthesis + calibration: y_hat for every (voxel, measurement) of the tile range.
 template <int K, int TPV, bool CAL>
 __global__ void __launch_bounds__(256) k_synth(const IterArgs a, const PlainArgs pa) {

@@ -131,12 +131,19 @@ cudaError_t l_prior(const IterArgs& a, const PlainArgs& p, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+cudaError_t l_fibers(const IterArgs& a, const int32_t* sov, int64_t V, float rel, float* dirs, float* fracs,
+                     uint8_t* peaks, cudaStream_t st) {
+  if (V <= 0) return cudaSuccess;
+  k_fibers<kK><<<nblocks(V, 128), 128, 0, st>>>(a, sov, V, rel, dirs, fracs, peaks);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 #define PRISM_CAT2(a, b) a##b
 #define PRISM_CAT(a, b) PRISM_CAT2(a, b)
 const KernelSet& PRISM_CAT(kernels_k, PRISM_K)() {
-  static const KernelSet ks = {l_fused, l_fused_occupancy, l_transform, l_synth, l_adjoint, l_prior_prep, l_prior};
+  static const KernelSet ks = {l_fused, l_fused_occupancy, l_transform, l_synth, l_adjoint, l_prior_prep, l_prior, l_fibers};
   return ks;
 }
 

@@ -18,6 +18,8 @@ struct KernelSet {
                          cudaStream_t st);
   cudaError_t (*prior_prep)(const IterArgs& a, int tb, int te, cudaStream_t st);
   cudaError_t (*prior)(const IterArgs& a, const PlainArgs& p, cudaStream_t st);
+  cudaError_t (*fibers)(const IterArgs& a, const int32_t* slot_of_vox, int64_t V, float rel, float* dirs,
+                        float* fracs, uint8_t* peaks, cudaStream_t st);
 };
 
 const KernelSet& kernels_for_k(int K);

@@ -224,3 +224,23 @@ def test_stabilisers_26_connectivity_steps(tpv, loss, cal):
     th = f.params_host()
     assert float(np.max(np.abs(th - np.concatenate([t.numpy() for t in res.theta])))) < 3e-4
     f.close()
+
+
+
+def test_fiber_readout_matches_oracle_metrics():
+    """prism_get_fibers: directions, fractions and peak flags against the oracle's readout."""
+    vols = _problem(False)
+    K = 3
+    rng = np.random.default_rng(17)
+    inits = [(t + rng.normal(0, 0.8, t.shape)).astype(np.float32) for t in inits_for(vols, K, 17)]
+    f, _ = make_pair(vols, inits, K=K, patch_dim=4)
+    d, fr, pk = f.fibers(0.15)
+    th = np.concatenate(inits)
+    dref, fwm = M.fibers(th, K)
+    np.testing.assert_allclose(d, dref, rtol=0, atol=TOL_SIGNAL)
+    np.testing.assert_allclose(fr[:, 2:K + 2], fwm, rtol=TOL_SIGNAL, atol=1e-7)
+    np.testing.assert_allclose(fr.sum(1), 1.0, atol=TOL_SIGNAL)
+    share = fwm / fwm.sum(1, keepdims=True)
+    clear = np.abs(share - 0.15) > 1e-4          # away from the threshold the decision is unique
+    assert np.array_equal(pk[clear], M.peak_mask(fwm, 0.15)[clear])
+    f.close()
