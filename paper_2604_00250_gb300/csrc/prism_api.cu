@@ -94,6 +94,8 @@ struct prism_handle {
   int32_t *d_split_off = nullptr, *d_counters = nullptr;
   uint32_t *d_vcoord = nullptr, *d_vflag = nullptr;
   int64_t* d_row_off = nullptr;
+  int32_t* d_order = nullptr;          // [tab_rows] table position -> caller's measurement index
+  std::vector<int32_t> order;          // host copy
   MeasRow* d_table = nullptr;
   MeasPair* d_table2 = nullptr;
   int64_t tab2_pairs = 0;
@@ -371,6 +373,28 @@ int capture_graph(prism_handle* h, int iters, cudaGraphExec_t* out) {
 }
 
 // Host-side plan of volumes -> patches -> tiles, neighbours and flags.
+// Internal measurement order of one group, appended to `order` (table position -> the
+// caller's index). Without calibration the b = 0 measurements come first (stable), so that
+// the packed path can take their pairs without the fiber terms (every E of Eqs. 4-5 is 1 at
+// b = 0); with calibration, whose alpha_n / beta_n are indexed by measurement, the order is
+// the caller's. Returns the number of leading pairs whose two measurements have b = 0.
+static int32_t meas_order(const prism_volume& v, bool cal, std::vector<int32_t>& order) {
+  const int N = v.n_meas;
+  if (cal) {
+    for (int n = 0; n < N; ++n) order.push_back(n);
+    return 0;
+  }
+  int nz = 0;
+  for (int n = 0; n < N; ++n)
+    if (v.bvals[n] == 0.f) {
+      order.push_back(n);
+      ++nz;
+    }
+  for (int n = 0; n < N; ++n)
+    if (v.bvals[n] != 0.f) order.push_back(n);
+  return nz / 2;
+}
+
 struct Plan {
   std::vector<int32_t> slot_of_vox, vox_of_slot, nbr, slot_of_grid;
   std::vector<uint32_t> vcoord, vflag;
@@ -421,6 +445,7 @@ int build_plan(prism_handle* h, const prism_volume* vols, int n_vols, Plan& pl) 
     gr.inv_M = 1.f / static_cast<float>(gr.n_vox);
     gr.calib = h->cal ? 1 : 0;
     gr.table_off = static_cast<int32_t>(tab);
+    gr.nb0p = meas_order(v, h->cal, h->order);
     tab += v.n_meas;
     gr.table2_off = static_cast<int32_t>(h->tab2_pairs);
     h->tab2_pairs += ((v.n_meas + 3) & ~3) / 2;
@@ -611,6 +636,7 @@ int init_impl(prism_handle* h, const prism_volume* vols, int n_vols, cudaStream_
   RC(h->alloc(&h->d_vox_of_slot, Vp));
   RC(h->alloc(&h->d_slot_of_grid, pl.slot_of_grid.size()));
   RC(h->alloc(&h->d_row_off, h->V));
+  RC(h->alloc(&h->d_order, std::max<int64_t>(h->tab_rows, 1)));
   RC(h->alloc(&h->d_split_off, G));
   RC(h->alloc(&h->d_part2, static_cast<size_t>(tot_split) * h->max_e));
   RC(h->alloc(&h->d_counters, static_cast<size_t>(G) * nce));
@@ -652,6 +678,7 @@ int init_impl(prism_handle* h, const prism_volume* vols, int n_vols, cudaStream_
   RC(upload(h->d_vox_of_slot, pl.vox_of_slot, st));
   RC(upload(h->d_slot_of_grid, pl.slot_of_grid, st));
   RC(upload(h->d_row_off, pl.row_off, st));
+  RC(upload(h->d_order, h->order, st));
   RC(upload(h->d_split_off, split_off, st));
   fill_args(h);
   // per volume: b0 statistics, packing, table, sigma, parameters
@@ -671,7 +698,12 @@ int init_impl(prism_handle* h, const prism_volume* vols, int n_vols, cudaStream_
       sig = tmp_sig;
     }
     std::vector<uint8_t> isb0(N);
-    std::vector<float> bv(v.bvals, v.bvals + N), bvec(v.bvecs, v.bvecs + 3 * N);
+    std::vector<float> bv(N), bvec(3 * N);   // in table order
+    const int32_t* ord = h->order.data() + gr.table_off;
+    for (int n = 0; n < N; ++n) {
+      bv[n] = v.bvals[ord[n]];
+      for (int c = 0; c < 3; ++c) bvec[3 * n + c] = v.bvecs[3 * ord[n] + c];
+    }
     int nb0 = 0;
     for (int n = 0; n < N; ++n) {
       isb0[n] = v.bvals[n] <= 50.f;
@@ -691,7 +723,8 @@ int init_impl(prism_handle* h, const prism_volume* vols, int n_vols, cudaStream_
     RC(upload(d_bvec, bvec, st));
     CK(launch_b0_stats(sig, Vg, N, d_isb0, nb0, d_b0, d_part, d_bad, st));
     CK(launch_sigma_init(d_part, nbk, Vg, nb0, o.sigma_init, h->d_gparams + gr.gp_off, st));
-    CK(launch_pack(h->ia, sig, d_b0, h->d_vox_of_slot, h->vox0[g], gr.tile0, gr.tile0 + gr.ntiles, N, h->d_y, d_bad, st));
+    CK(launch_pack(h->ia, sig, d_b0, h->d_vox_of_slot, h->d_order + gr.table_off, h->vox0[g], gr.tile0,
+                   gr.tile0 + gr.ntiles, N, h->d_y, d_bad, st));
     CK(launch_table(d_bv, d_bvec, N, h->d_table + gr.table_off, st));
     CK(launch_pair_table(h->d_table + gr.table_off, N, h->d_table2 + gr.table2_off, st));
     if (v.init) {
@@ -1021,7 +1054,7 @@ extern "C" int prism_forward(prism_handle* h, const float* theta, const float* g
   CK(launch_group_reduce(a, h->ga, 1, st));
   CK(launch_group_adam(a, h->ga, 1, st));
   if (loss) CK(cudaMemcpyAsync(loss, h->d_gloss, sizeof(double) * h->G, cudaMemcpyDeviceToDevice, st));
-  if (yhat) CK(launch_gather_yhat(h->d_yhat, a, h->d_vox_of_slot, h->d_row_off, yhat, st));
+  if (yhat) CK(launch_gather_yhat(h->d_yhat, a, h->d_vox_of_slot, h->d_row_off, h->d_order, yhat, st));
   h->forward_done = true;
   return PRISM_OK;
 }

@@ -58,8 +58,8 @@ __global__ void k_sigma_init(const double* part, int nblocks, int64_t V, int nb0
 }
 
 __global__ void k_pack(const IterArgs a, const float* __restrict__ sig, const float* __restrict__ b0mean,
-                       const int32_t* __restrict__ vox_of_slot, int64_t vox0, int tile_begin, int N,
-                       float* __restrict__ ypack) {
+                       const int32_t* __restrict__ vox_of_slot, const int32_t* __restrict__ order, int64_t vox0,
+                       int tile_begin, int N, float* __restrict__ ypack) {
   const int t = tile_begin + blockIdx.x;
   const Tile tl = a.tiles[t];
   const int NP = (N + 3) & ~3;
@@ -68,7 +68,7 @@ __global__ void k_pack(const IterArgs a, const float* __restrict__ sig, const fl
     float val = 0.f;
     if (vl < tl.count && n < N) {
       const int64_t v = vox_of_slot[tl.slot0 + vl] - vox0;
-      val = sig[v * N + n] / b0mean[v];
+      val = sig[v * N + order[n]] / b0mean[v];
     }
     ypack[ypos(tl, n, vl, a.VW)] = val;
   }
@@ -172,13 +172,14 @@ __global__ void k_default_init(const int32_t* __restrict__ slot_of_vox, int64_t 
 
 __global__ void k_gather_yhat(const float* __restrict__ ypack, const IterArgs a,
                               const int32_t* __restrict__ vox_of_slot, const int64_t* __restrict__ row_off,
-                              float* __restrict__ out) {
+                              const int32_t* __restrict__ order, float* __restrict__ out) {
   const Tile tl = a.tiles[blockIdx.x];
+  const int32_t* ord = order + a.groups[tl.group].table_off;
   for (int e = threadIdx.x; e < tl.n_meas * a.TV; e += blockDim.x) {
     const int n = e / a.TV, vl = e - n * a.TV;
     if (vl >= tl.count) continue;
     const int64_t v = vox_of_slot[tl.slot0 + vl];
-    out[row_off[v] + n] = ypack[ypos(tl, n, vl, a.VW)];
+    out[row_off[v] + ord[n]] = ypack[ypos(tl, n, vl, a.VW)];
   }
 }
 
@@ -463,11 +464,11 @@ cudaError_t launch_sigma_init(const double* part, int nblocks, int64_t V, int nb
   return cudaGetLastError();
 }
 cudaError_t launch_pack(const IterArgs& a, const float* sig, const float* b0mean, const int32_t* vox_of_slot,
-                        int64_t vox0, int tile_begin, int tile_end, int N, float* ypack, int* bad,
-                        cudaStream_t st) {
+                        const int32_t* order, int64_t vox0, int tile_begin, int tile_end, int N, float* ypack,
+                        int* bad, cudaStream_t st) {
   (void)bad;
   if (tile_end <= tile_begin) return cudaSuccess;
-  k_pack<<<tile_end - tile_begin, 256, 0, st>>>(a, sig, b0mean, vox_of_slot, vox0, tile_begin, N, ypack);
+  k_pack<<<tile_end - tile_begin, 256, 0, st>>>(a, sig, b0mean, vox_of_slot, order, vox0, tile_begin, N, ypack);
   return cudaGetLastError();
 }
 cudaError_t launch_table(const float* bvals, const float* bvecs, int N, MeasRow* rows, cudaStream_t st) {
@@ -498,8 +499,8 @@ cudaError_t launch_default_init(const int32_t* sov, int64_t V, int K, int Vpad, 
   return cudaGetLastError();
 }
 cudaError_t launch_gather_yhat(const float* ypack, const IterArgs& a, const int32_t* vos, const int64_t* roff,
-                               float* out, cudaStream_t st) {
-  k_gather_yhat<<<a.ntiles, 256, 0, st>>>(ypack, a, vos, roff, out);
+                               const int32_t* order, float* out, cudaStream_t st) {
+  k_gather_yhat<<<a.ntiles, 256, 0, st>>>(ypack, a, vos, roff, order, out);
   return cudaGetLastError();
 }
 cudaError_t launch_adam_constants(const IterArgs& a, cudaStream_t st) {

@@ -62,7 +62,7 @@ struct GroupDev {
   int32_t calib;       // calibration learned for this group
   int64_t grid_off;    // offset of the group's [nx][ny][nz] slot map
   int32_t table2_off;  // first MeasPair of the group
-  int32_t pad;
+  int32_t nb0p;        // leading table pairs whose two measurements both have b = 0 (see meas_order)
 };
 
 // Kernel arguments shared by the iteration kernels (passed by value).

@@ -449,6 +449,35 @@ __device__ __forceinline__ void step2(const VoxP<K>& D, const MeasPair& R, float
   }
 }
 
+// Packed steps over n pairs of b = 0 measurements: every compartment signal of Eqs. 4-5 is
+// exactly 1 there (c no longer matters), so y_hat = S0 * sum of the fractions, and each
+// accumulator sum_n r E gains sum_n r while the direction terms gain nothing. The sum of the
+// fractions is formed again at each pair (a loop-carried copy costs registers the main loop
+// needs).
+template <int K>
+__device__ __forceinline__ void step2_b0(const VoxP<K>& D, const float2* __restrict__ yc2, int stride, int n,
+                                         AccP<K>& A) {
+  float2 rs = make_float2(0.f, 0.f);
+#pragma unroll 1
+  for (int i = 0; i < n; ++i) {
+    float2 T = __fadd2_rn(D.fcsf, D.fgm);
+    T = __fadd2_rn(T, D.fres);
+#pragma unroll
+    for (int k = 0; k < K; ++k) T = __fadd2_rn(T, __fadd2_rn(D.ffin[k], D.fomf[k]));
+    const float2 r = __ffma2_rn(D.nS0, T, yc2[i * stride]);   // y - y_hat
+    A.l1 = __ffma2_rn(r, r, A.l1);
+    rs = __fadd2_rn(rs, r);
+  }
+  A.gcsf = __fadd2_rn(A.gcsf, rs);
+  A.ggm = __fadd2_rn(A.ggm, rs);
+  A.gres = __fadd2_rn(A.gres, rs);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    A.gwa[k] = __fadd2_rn(A.gwa[k], rs);
+    A.gwb[k] = __fadd2_rn(A.gwb[k], rs);
+  }
+}
+
 // Fold packed accumulators into the scalar ones (dJ/dS0 from the compartment sums:
 // sum_n q T = f_csf sum q E_csf + ... + sum_k (f_k f_in sum q e1 + f_k (1-f_in) sum q p)).
 template <int K>
@@ -526,9 +555,23 @@ __device__ __forceinline__ void block_reduce3(double v0, double v1, double v2, d
 // warp finishes a tile it already fetches the first chunks of the CTA's next tile.
 // The measurement table and the bias grid arrive by bulk copy when the group changes.
 // ===========================================================================
-constexpr int kChunk = 16;    // measurements per ring stage
-constexpr int kStages = 4;    // ring depth per warp
+constexpr int kChunk = 32;    // measurements per ring stage
+constexpr int kStages = 2;    // ring depth per warp
 constexpr int kFusedThreads = 128;
+
+// Adam / Rprop state of one voxel. Every load is issued before any store of the update (the
+// stores could alias the loads as far as the compiler knows, which would serialise one memory
+// round trip per parameter).
+template <int Q>
+__device__ __forceinline__ void load_moments(const IterArgs& a, int slot, bool writer, float (&mq)[Q],
+                                             float (&vq)[Q]) {
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const size_t ix = static_cast<size_t>(q) * a.Vpad + slot;
+    mq[q] = writer ? a.m[ix] : 0.f;
+    vq[q] = writer ? a.v[ix] : 0.f;
+  }
+}
 
 // Last CTA of an uncalibrated fused iteration: fixed-order sums of the tiles' partials per
 // group (strided over threads, then a fixed tree), the objective and its history, Adam on
@@ -599,6 +642,7 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_iter_fused(const IterArgs 
   constexpr int NW = kFusedThreads / 32;
   constexpr int VW = 32 / TPV;              // voxels per warp
   constexpr bool PACKED = (TPV == 1) && (LOSS == kLossMSE) && !CAL;
+  constexpr bool HOIST = PACKED && K <= 3;
   static_assert(kChunk % TPV == 0, "chunk must split evenly across the voxel's lanes");
   extern __shared__ __align__(16) unsigned char smem[];
   const int Vp = a.Vpad;
@@ -751,11 +795,15 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_iter_fused(const IterArgs 
       if constexpr (PACKED) {
         const float2* __restrict__ yc2 = reinterpret_cast<const float2*>(ring + s * (kChunk * VW)) + lv;
         const MeasPair* __restrict__ tab2 = reinterpret_cast<const MeasPair*>(s_tab) + j * (kChunk / 2);
-        if (act && cnt == kChunk) {
+        // leading pairs of b = 0 measurements (the group's table starts with them)
+        const int i0 = max(0, min(kChunk / 2, gr.nb0p - j * (kChunk / 2)));
+        if (act && cnt == kChunk && i0 == 0) {
 #pragma unroll 2
           for (int i = 0; i < kChunk / 2; ++i) step2<K, false>(DP, tab2[i], yc2[i * VW], make_float2(1.f, 1.f), AP);
         } else if (act) {
-          for (int i = 0; i < (cnt + 1) / 2; ++i)
+          if (i0 > 0) step2_b0<K>(DP, yc2, VW, i0, AP);
+#pragma unroll 1
+          for (int i = i0; i < (cnt + 1) / 2; ++i)
             step2<K, true>(DP, tab2[i], yc2[i * VW], make_float2(1.f, (2 * i + 1 < cnt) ? 1.f : 0.f), AP);
         }
         __syncwarp();
@@ -794,12 +842,14 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_iter_fused(const IterArgs 
       ++g;
     }
     base += nch;
-    // voxel transforms again (not kept live across the loop)
-    {
-      float th[Q];
-      load_theta<K>(a.theta, Vp, slot, act, th);
-      transform<K>(th, P);
-    }
+    // voxel transforms again (not kept live across the loop). Where registers allow (HOIST),
+    // the raw parameters and the moments are read here, once, so that their latency overlaps
+    // the epilogue's math; otherwise they are re-read before the update.
+    const bool writer = act && (js == 0);
+    float th[Q], mq[Q], vq[Q];
+    load_theta<K>(a.theta, Vp, slot, act, th);
+    if constexpr (HOIST) load_moments<Q>(a, slot, writer, mq, vq);
+    transform<K>(th, P);
     if constexpr (PACKED) accp_fold<K>(P, AP, A);
     acc_reduce_tpv<K, TPV>(A);
 
@@ -820,21 +870,13 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_iter_fused(const IterArgs 
       const uint32_t fl = act ? a.vflag[slot] : 0u;
       ploss += tv_term(s_blr, cx, cy, cz, gr, fl, B, a.w_tv * gr.inv_M, a.tv_eps, gUv);
     }
-    // ---- chain rule and Adam (raw parameters re-read: they are not kept live across the loop)
-    float th[Q];
-    load_theta<K>(a.theta, Vp, slot, act, th);
+    // ---- chain rule and the update
+    if constexpr (!HOIST) {
+      load_theta<K>(a.theta, Vp, slot, act, th);
+      load_moments<Q>(a, slot, writer, mq, vq);
+    }
     float gq[Q];
     chain_raw<K>(P, gS0, gf, gd, gfin, gq);
-    const bool writer = act && (js == 0);
-    // Adam: every moment load is issued before any store (the stores could alias the loads
-    // as far as the compiler knows, which would serialise one memory round trip per parameter)
-    float mq[Q], vq[Q];
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-      const size_t ix = static_cast<size_t>(q) * Vp + slot;
-      mq[q] = writer ? a.m[ix] : 0.f;
-      vq[q] = writer ? a.v[ix] : 0.f;
-    }
     if (a.optimizer == 0) {
 #pragma unroll
       for (int q = 0; q < Q; ++q) {

@@ -57,8 +57,8 @@ cudaError_t launch_b0_stats(const float* sig, int64_t V, int N, const uint8_t* i
 cudaError_t launch_sigma_init(const double* part, int nblocks, int64_t V, int nb0, float sigma_fallback,
                               float* sigma_log_out, cudaStream_t st);
 cudaError_t launch_pack(const IterArgs& a, const float* sig, const float* b0mean, const int32_t* vox_of_slot,
-                        int64_t vox0, int tile_begin, int tile_end, int N, float* ypack, int* bad,
-                        cudaStream_t st);
+                        const int32_t* order, int64_t vox0, int tile_begin, int tile_end, int N, float* ypack,
+                        int* bad, cudaStream_t st);
 cudaError_t launch_table(const float* bvals, const float* bvecs, int N, MeasRow* rows, cudaStream_t st);
 cudaError_t launch_pair_table(const MeasRow* rows, int N, MeasPair* out, cudaStream_t st);
 cudaError_t launch_scatter_params(const float* in, const int32_t* slot_of_vox, int64_t V, int Q, int Vpad,
@@ -68,7 +68,7 @@ cudaError_t launch_gather_params(const float* theta, const int32_t* slot_of_vox,
 cudaError_t launch_default_init(const int32_t* slot_of_vox, int64_t V, int K, int Vpad, uint64_t seed,
                                 float* theta, cudaStream_t st);
 cudaError_t launch_gather_yhat(const float* ypack, const IterArgs& a, const int32_t* vox_of_slot,
-                               const int64_t* yhat_row_off, float* out, cudaStream_t st);
+                               const int64_t* yhat_row_off, const int32_t* order, float* out, cudaStream_t st);
 cudaError_t launch_table_refresh(const GroupArgs& g, const IterArgs& a, cudaStream_t st);
 cudaError_t launch_adam_constants(const IterArgs& a, cudaStream_t st);
 

@@ -244,3 +244,56 @@ def test_fiber_readout_matches_oracle_metrics():
     clear = np.abs(share - 0.15) > 1e-4          # away from the threshold the decision is unique
     assert np.array_equal(pk[clear], M.peak_mask(fwm, 0.15)[clear])
     f.close()
+
+
+def _interleave_b0(vols, seed):
+    """The same volumes with their measurements in a seeded random order (b = 0 volumes
+    scattered through the scheme, as scanners interleave them)."""
+    out = []
+    for i, v in enumerate(vols):
+        perm = np.random.default_rng(seed + i).permutation(v.n_meas)
+        out.append(P.Volume(mask=v.mask, signal=np.ascontiguousarray(np.asarray(v.signal)[:, perm]),
+                            bvals=v.bvals[perm].copy(), bvecs=v.bvecs[perm].copy(), gt=v.gt))
+    return out
+
+
+@pytest.mark.parametrize("loss,tpv", [("mse", 1), ("nll", 4)])
+def test_interleaved_b0_scheme(loss, tpv):
+    """Without calibration the library moves the b = 0 measurements to the front of its table
+    (the packed path then takes their pairs without the fiber terms); y_hat comes back in the
+    caller's order, and a permuted scheme gives the oracle's objective, gradient and steps."""
+    vols = _interleave_b0(_problem(False), 11)
+    assert any(np.flatnonzero(v.bvals == 0).max() > 8 for v in vols)
+    K = 3
+    rng = np.random.default_rng(2)
+    inits = [th + rng.normal(0, 0.3, th.shape).astype(np.float32) for th in inits_for(vols, K, 7)]
+    kw = dict(K=K, loss=loss, patch_dim=4, threads_per_voxel=tpv, lam_sp=0.01, lam_dir=0.005)
+    f, ovs = make_pair(vols, inits, **kw)
+    packed = _perturb_groups(f, rng, False, loss)
+    gps = split_groups(packed, f)
+    loss_g, yhat = f.forward(want_yhat=True)
+    gth, _ = f.backward()
+    torch.cuda.synchronize()
+    yhat, gth = yhat.cpu().numpy(), gth.cpu().numpy()
+    pos = vpos = 0
+    for gi, ov in enumerate(ovs):
+        th = torch.as_tensor(inits[gi]).double()
+        yref, _ = O.predict(ov, th, gps[gi])
+        n = ov.n_vox * ov.n_meas
+        assert signal_rel(yhat[pos:pos + n].reshape(ov.n_vox, ov.n_meas), yref.numpy()) <= TOL_SIGNAL
+        pos += n
+        J, _, g, _ = O.value_and_grad(ov, th, gps[gi])
+        assert abs(float(loss_g[gi]) - float(J)) <= TOL_LOSS * abs(float(J))
+        for name, sl in block_slices(K).items():
+            assert normwise(gth[vpos:vpos + ov.n_vox, sl], g[:, sl].numpy()) <= TOL_GRAD, (gi, name)
+        vpos += ov.n_vox
+    f.close()
+    # three fused iterations against the oracle's
+    f, ovs = make_pair(vols, inits, **kw)
+    f.step(3)
+    f.sync()
+    res = O.fit(ovs, [torch.as_tensor(t).double() for t in inits], 3)
+    np.testing.assert_allclose(f.loss_history(), res.loss_history, rtol=1e-5)
+    ref = np.concatenate([t.numpy() for t in res.theta])
+    assert float(np.max(np.abs(f.params_host() - ref))) < 3e-4
+    f.close()
