@@ -109,6 +109,43 @@ __device__ __forceinline__ void store_xf(float* __restrict__ xf, int Vp, int slo
     for (int c = 0; c < 3; ++c) xf[static_cast<size_t>(K + 3 + 3 * k + c) * Vp + slot] = P.d[k][c];
 }
 
+// One neighbour x of the voxel at `slot` in the Huber-Laplacian (subtracts x's rho'(u)/|N|
+// from hs) and the directional-continuity term (value and direction gradient). x < 0 (no
+// neighbour) contributes nothing; its loads then read the voxel's own rows.
+template <int K>
+__device__ __forceinline__ void nbr_term(const IterArgs& a, const Vox<K>& P, int x, int slot, float inv_n,
+                                         float wdir, const float* __restrict__ xf_cur, float (&hs)[K + 3],
+                                         float& val, float (&gd)[K][3]) {
+  constexpr int NF = K + 3;
+  const int Vp = a.Vpad;
+  const bool ok = x >= 0;
+  const int xx = ok ? x : slot;
+  if (a.lam_sp > 0.f) {
+#pragma unroll
+    for (int c = 0; c < NF; ++c) {
+      const float h = a.hsp[static_cast<size_t>(c) * Vp + xx];
+      hs[c] -= ok ? h : 0.f;
+    }
+  }
+  if (a.lam_dir > 0.f) {
+    const int nx_cnt = max(1, static_cast<int>((a.vflag[xx] >> 8) & 31));
+    const float wgt = inv_n + 1.f / static_cast<float>(nx_cnt);
+    const float wv = ok ? wdir * inv_n : 0.f;
+    const float ws = ok ? -2.f * wdir * wgt : 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      float dx[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) dx[q] = xf_cur[static_cast<size_t>(K + 3 + 3 * k + q) * Vp + xx];
+      const float c = P.d[k][0] * dx[0] + P.d[k][1] * dx[1] + P.d[k][2] * dx[2];
+      val = fmaf(wv, 1.f - c * c, val);
+      const float sc = ws * c;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) gd[k][q] = fmaf(sc, dx[q], gd[k][q]);
+    }
+  }
+}
+
 // Priors of Sec. 2.4 at one voxel: value, and gradient added to gS0 / gf / gd (transformed
 // space). Repulsion, sparsity, orphan-WM suppression and fiber ordering are local; the
 // Huber-Laplacian uses the precomputed rho'(u)/|N| of the voxel and its neighbours;
@@ -184,28 +221,17 @@ __device__ __forceinline__ float priors(const IterArgs& a, const Vox<K>& P, int 
 #pragma unroll
         for (int c = 0; c < NF; ++c) hs[c] = a.hsp[static_cast<size_t>(c) * Vp + slot] * static_cast<float>(ncnt);
       }
-      for (int e = 0; e < a.n_nbr; ++e) {
-        const int x = a.nbr[static_cast<size_t>(e) * Vp + slot];
-        if (x < 0) continue;
-        if (a.lam_sp > 0.f) {
+      if (a.n_nbr == 6) {
+        // face neighbours: every index first, then every neighbour's data (a missing
+        // neighbour reads the voxel's own row with weight 0), so that the gathers overlap
+        int xs[6];
 #pragma unroll
-          for (int c = 0; c < NF; ++c) hs[c] -= a.hsp[static_cast<size_t>(c) * Vp + x];
-        }
-        if (a.lam_dir > 0.f) {
-          const int nx_cnt = (a.vflag[x] >> 8) & 31;
-          const float wgt = inv_n + 1.f / static_cast<float>(nx_cnt);
+        for (int e = 0; e < 6; ++e) xs[e] = a.nbr[static_cast<size_t>(e) * Vp + slot];
 #pragma unroll
-          for (int k = 0; k < K; ++k) {
-            float dx[3];
-#pragma unroll
-            for (int q = 0; q < 3; ++q) dx[q] = xf_cur[static_cast<size_t>(K + 3 + 3 * k + q) * Vp + x];
-            const float c = P.d[k][0] * dx[0] + P.d[k][1] * dx[1] + P.d[k][2] * dx[2];
-            val = fmaf(wdir * inv_n, 1.f - c * c, val);
-            const float sc = -2.f * wdir * c * wgt;
-#pragma unroll
-            for (int q = 0; q < 3; ++q) gd[k][q] = fmaf(sc, dx[q], gd[k][q]);
-          }
-        }
+        for (int e = 0; e < 6; ++e) nbr_term<K>(a, P, xs[e], slot, inv_n, wdir, xf_cur, hs, val, gd);
+      } else {
+        for (int e = 0; e < a.n_nbr; ++e)
+          nbr_term<K>(a, P, a.nbr[static_cast<size_t>(e) * Vp + slot], slot, inv_n, wdir, xf_cur, hs, val, gd);
       }
       if (a.lam_sp > 0.f) {
 #pragma unroll
@@ -691,6 +717,7 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_iter_fused(const IterArgs 
   };
 
   while (t < a.ntiles) {
+    // next tile: round-robin while static tiles remain (no atomic, no barrier), then the queue
     if (tid == 0) s_next = atomicAdd(a.queue, 1);
     __syncthreads();
     const int t_next = s_next;
