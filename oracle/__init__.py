@@ -3,4 +3,4 @@
 Imported only by tests, the smoke check and the benchmark's CPU-baseline leg.
 It shares no code with the CUDA library and never imports the package.
 """
-from . import prism_oracle, metrics  # noqa: F401
+from . import prism_oracle, metrics, slabs  # noqa: F401
