@@ -146,6 +146,33 @@ int prism_get_fibers(prism_handle* h, float* dirs, float* fracs, uint8_t* peaks,
                      int32_t mem, void* stream);
 
 /*
+ * Whole-volume fit in overlapping slabs (Sec. 3 "Configuration": the whole brain is fitted
+ * as 30-slice slabs with a 5-slice overlap, stitched by weighted averaging). `vol` is split
+ * along its last axis into slabs of `slab` slices advancing by slab - overlap, the last one
+ * reaching the last slice; every non-empty slab becomes one volume of a handle initialised as
+ * by prism_fit_init (its own sigma and calibration; neighbour priors stay inside the slab).
+ * The slab signals (and `init` rows) are gathered on the device from vol->signal in `vol->mem`
+ * memory; the caller's buffers are not kept. Step the handle as usual, then read the
+ * whole-volume maps with prism_stitch_slabs. E_INVALID_ARG for slab < 1, overlap < 0 or
+ * 2 * overlap > slab, E_SHAPE for an empty mask, plus every error of prism_fit_init.
+ */
+int prism_fit_init_slabs(const prism_volume* vol, int32_t slab, int32_t overlap, const prism_options* opt,
+                         void* stream, prism_handle** out);
+
+/*
+ * Whole-volume maps of a handle made by prism_fit_init_slabs, in the original volume's mask
+ * order and `mem` memory: S0 [V], fractions [V][K+3] ([csf, gm, wm_1..wm_K, res]), f_intra [V],
+ * unit directions [V][K][3]; any output may be NULL. A voxel in one slab takes that slab's
+ * estimate. In an overlap the later slab's weight ramps linearly across the overlapping
+ * slices, w = (z - z0 + 1/2) / overlap; its fibers are matched to the earlier slab's by the
+ * permutation maximising sum_k |d_k . d'_pi(k)| (FP64, first maximum in lexicographic order),
+ * flipped into the same hemisphere, and S0, fractions, f_intra and directions are averaged
+ * (directions renormalised). E_STATE for a handle not made by prism_fit_init_slabs.
+ */
+int prism_stitch_slabs(prism_handle* h, float* s0, float* fracs, float* fin, float* dirs, int32_t mem,
+                       void* stream);
+
+/*
  * Packed group parameters. Group g occupies [off[4g], off[4g+4]) of the packed
  * float array: sigma_log at off[4g], alpha[N_g] at off[4g+1], beta[N_g] at
  * off[4g+2], b_lr[8][8][8] (C order) at off[4g+3]; off[4G] = total. `off` is a

@@ -118,14 +118,22 @@ def _volumes_array(volumes, keep):
 class Fitter:
     """One PRISM fit (a handle of the C library) over a batch of volumes."""
 
-    def __init__(self, volumes, opts=None, stream=None, **kw):
+    def __init__(self, volumes, opts=None, stream=None, slabs=None, **kw):
+        """`slabs=(slab, overlap)` fits one whole volume as overlapping slabs along its last
+        axis (prism_fit_init_slabs); `stitch()` then returns the whole-volume maps."""
         lib = _lib.load()
         self._lib = lib
         self.opts = opts if opts is not None else options(**kw)
         keep = []
-        arr, n = _volumes_array(volumes, keep)
         h = ctypes.c_void_p()
-        _lib.check(lib.prism_fit_init(arr, n, ctypes.byref(self.opts), _stream_ptr(stream), ctypes.byref(h)))
+        if slabs is not None:
+            vol = volumes[0] if isinstance(volumes, (list, tuple)) else volumes
+            vs = _volume_struct(vol, keep)
+            _lib.check(lib.prism_fit_init_slabs(ctypes.byref(vs), int(slabs[0]), int(slabs[1]),
+                                                ctypes.byref(self.opts), _stream_ptr(stream), ctypes.byref(h)))
+        else:
+            arr, n = _volumes_array(volumes, keep)
+            _lib.check(lib.prism_fit_init(arr, n, ctypes.byref(self.opts), _stream_ptr(stream), ctypes.byref(h)))
         self._h = h
         V, G, Q, GP, it = (ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64(),
                            ctypes.c_int64())
@@ -134,8 +142,14 @@ class Fitter:
         self.n_vox, self.n_groups, self.Q, self.n_group_params = V.value, G.value, Q.value, GP.value
         self.K = int(self.opts.K)
         vols = volumes if isinstance(volumes, (list, tuple)) else [volumes]
-        self.n_meas = [int(np.asarray(v.bvals).shape[0]) for v in vols]
-        self.yhat_len = sum(int(np.asarray(v.mask).astype(bool).sum()) * n for v, n in zip(vols, self.n_meas))
+        if slabs is not None:
+            N = int(np.asarray(vols[0].bvals).shape[0])
+            self.n_meas = [N] * self.n_groups
+            self.yhat_len = self.n_vox * N
+            self.n_out = int(np.asarray(vols[0].mask).astype(bool).sum())
+        else:
+            self.n_meas = [int(np.asarray(v.bvals).shape[0]) for v in vols]
+            self.yhat_len = sum(int(np.asarray(v.mask).astype(bool).sum()) * n for v, n in zip(vols, self.n_meas))
 
     # -- lifecycle -----------------------------------------------------------
     def close(self):
@@ -189,6 +203,18 @@ class Fitter:
         _lib.check(self._lib.prism_set_params(self._h, ctypes.c_void_p(t.data_ptr()), MEM_DEVICE,
                                               _stream_ptr(stream)))
         torch.cuda.current_stream().synchronize()
+
+    def stitch(self):
+        """Whole-volume maps of a slab fit: (S0 [V], fractions [V, K+3], f_intra [V],
+        unit directions [V, K, 3]) in the volume's mask order, numpy float32."""
+        V, K = self.n_out, self.K
+        s0 = np.empty(V, np.float32)
+        fr = np.empty((V, K + 3), np.float32)
+        fi = np.empty(V, np.float32)
+        d = np.empty((V, K, 3), np.float32)
+        _lib.check(self._lib.prism_stitch_slabs(self._h, s0.ctypes.data, fr.ctypes.data, fi.ctypes.data,
+                                                d.ctypes.data, MEM_HOST, _stream_ptr(None)))
+        return s0, fr, fi, d
 
     def fibers(self, rel_thresh=0.15):
         """(unit directions [V, K, 3], fractions [V, K+3], peak flags [V, K]) as numpy arrays."""

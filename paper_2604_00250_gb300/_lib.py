@@ -18,6 +18,7 @@ EXPORTS = [
     "prism_set_groups", "prism_get_loss", "prism_forward", "prism_backward", "prism_state_size",
     "prism_get_state", "prism_set_state", "prism_fit", "prism_fit_destroy", "prism_last_error",
     "prism_profile", "prism_grad_noalloc", "prism_microbench", "prism_get_fibers",
+    "prism_fit_init_slabs", "prism_stitch_slabs",
 ]
 
 
@@ -93,6 +94,8 @@ def load():
         "prism_profile": (ctypes.c_int, [vp, i32, vp, vp]),
         "prism_microbench": (ctypes.c_int, [i32, vp, vp]),
         "prism_get_fibers": (ctypes.c_int, [vp, vp, vp, vp, ctypes.c_float, i32, vp]),
+        "prism_fit_init_slabs": (ctypes.c_int, [vp, i32, i32, vp, vp, vp]),
+        "prism_stitch_slabs": (ctypes.c_int, [vp, vp, vp, vp, vp, i32, vp]),
         "prism_grad_noalloc": (ctypes.c_int, [vp, vp, vp, vp, i64, i32, i32, ctypes.c_float, ctypes.c_float,
                                               ctypes.c_float, vp, vp, vp]),
     }

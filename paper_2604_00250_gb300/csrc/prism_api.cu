@@ -95,6 +95,11 @@ struct prism_handle {
   uint32_t *d_vcoord = nullptr, *d_vflag = nullptr;
   int64_t* d_row_off = nullptr;
   int32_t* d_order = nullptr;          // [tab_rows] table position -> caller's measurement index
+  // slab fits (prism_fit_init_slabs): per voxel of the whole volume, its source voxel(s) in
+  // the handle and the weight of the second source
+  bool slabbed = false;
+  std::vector<int64_t> st_src0, st_src1;
+  std::vector<float> st_w1;
   std::vector<int32_t> order;          // host copy
   MeasRow* d_table = nullptr;
   MeasPair* d_table2 = nullptr;
@@ -1203,6 +1208,183 @@ extern "C" int prism_set_state(prism_handle* h, const void* host_buf, int64_t by
   CK(cudaStreamSynchronize(st));
   h->iters = hd.step;
   h->forward_done = false;
+  return PRISM_OK;
+}
+
+namespace {
+// Device buffer released on scope exit (temporaries of the slab entry points).
+struct DevTmp {
+  void* p = nullptr;
+  ~DevTmp() {
+    if (p) cudaFree(p);
+  }
+  template <typename T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+}  // namespace
+
+extern "C" int prism_fit_init_slabs(const prism_volume* vol, int32_t slab, int32_t overlap, const prism_options* opt,
+                                    void* stream, prism_handle** out) {
+  g_err.clear();
+  if (!out) return fail(PRISM_E_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!vol) return fail(PRISM_E_INVALID_ARG, "vol is NULL");
+  if (slab < 1 || overlap < 0 || 2 * overlap > slab)
+    return fail(PRISM_E_INVALID_ARG, "need slab >= 1 and 0 <= overlap <= slab / 2");
+  RC(validate_volume(*vol, 0));
+  prism_options o;
+  if (opt) o = *opt;
+  else prism_default_options(&o);
+  RC(validate_options(o));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int nx = vol->nx, ny = vol->ny, nz = vol->nz, N = vol->n_meas, Q = 4 * o.K + 5;
+  // slabs along the last axis, stride slab - overlap, the last one reaching the last slice
+  std::vector<int> z0s, z1s;
+  for (int z0 = 0;; z0 += slab - overlap) {
+    z0s.push_back(z0);
+    z1s.push_back(std::min(z0 + slab, nz));
+    if (z1s.back() >= nz) break;
+  }
+  const int S = static_cast<int>(z0s.size());
+  // whole-volume mask order (C order) -> per-slab mask order (the same relative order)
+  std::vector<std::vector<int64_t>> rows(S);
+  std::vector<std::vector<uint8_t>> sub(S);
+  for (int s = 0; s < S; ++s) sub[s].assign(static_cast<size_t>(nx) * ny * (z1s[s] - z0s[s]), 0);
+  std::vector<int64_t> src0, src1;
+  std::vector<int32_t> slab0, slab1;
+  std::vector<float> w1;
+  int64_t v = 0;
+  for (int x = 0; x < nx; ++x)
+    for (int y = 0; y < ny; ++y)
+      for (int z = 0; z < nz; ++z) {
+        if (!vol->mask[(static_cast<int64_t>(x) * ny + y) * nz + z]) continue;
+        int first = -1;
+        int64_t i0 = -1, i1 = -1;
+        float wt = 0.f;
+        for (int s = 0; s < S; ++s) {
+          if (z < z0s[s] || z >= z1s[s]) continue;
+          const int zl = z - z0s[s];
+          sub[s][(static_cast<size_t>(x) * ny + y) * (z1s[s] - z0s[s]) + zl] = 1;
+          const int64_t idx = static_cast<int64_t>(rows[s].size());
+          rows[s].push_back(v);
+          if (first < 0) {
+            first = s;
+            i0 = idx;
+          } else {
+            i1 = idx;
+            // linear ramp across the overlap of slabs first and s
+            wt = (static_cast<float>(z - z0s[s]) + 0.5f) / static_cast<float>(z1s[first] - z0s[s]);
+          }
+        }
+        slab0.push_back(first);
+        src0.push_back(i0);
+        slab1.push_back(i1 >= 0 ? first + 1 : -1);
+        src1.push_back(i1);
+        w1.push_back(wt);
+        ++v;
+      }
+  const int64_t V = v;
+  if (V == 0) return fail(PRISM_E_SHAPE, "the mask is empty");
+  // non-empty slabs become the handle's volumes; handle voxel = vox0[g] + index in the slab
+  std::vector<int> gidx(S, -1);
+  std::vector<int64_t> vox0;
+  int G = 0;
+  int64_t acc = 0;
+  for (int s = 0; s < S; ++s)
+    if (!rows[s].empty()) {
+      gidx[s] = G++;
+      vox0.push_back(acc);
+      acc += static_cast<int64_t>(rows[s].size());
+    }
+  for (int64_t i = 0; i < V; ++i) {
+    src0[i] += vox0[gidx[slab0[i]]];
+    if (src1[i] >= 0) src1[i] += vox0[gidx[slab1[i]]];
+  }
+  // whole-volume signal (and initial parameters) on the device, then one gathered copy per slab
+  DevTmp dsig, dinit, drows;
+  const float* sig = vol->signal;
+  const float* init = vol->init;
+  if (vol->mem == PRISM_MEM_HOST) {
+    CK(cudaMalloc(&dsig.p, sizeof(float) * V * N));
+    CK(cudaMemcpyAsync(dsig.p, vol->signal, sizeof(float) * V * N, cudaMemcpyHostToDevice, st));
+    sig = dsig.as<float>();
+    if (init) {
+      CK(cudaMalloc(&dinit.p, sizeof(float) * V * Q));
+      CK(cudaMemcpyAsync(dinit.p, vol->init, sizeof(float) * V * Q, cudaMemcpyHostToDevice, st));
+      init = dinit.as<float>();
+    }
+  }
+  CK(cudaMalloc(&drows.p, sizeof(int64_t) * acc));
+  std::vector<DevTmp> ssig(G), sinit(G);
+  std::vector<prism_volume> vols(G);
+  for (int s = 0; s < S; ++s) {
+    const int g = gidx[s];
+    if (g < 0) continue;
+    const int64_t n = static_cast<int64_t>(rows[s].size());
+    int64_t* dr = drows.as<int64_t>() + vox0[g];
+    CK(cudaMemcpyAsync(dr, rows[s].data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMalloc(&ssig[g].p, sizeof(float) * n * N));
+    CK(launch_gather_rows(sig, dr, n, N, ssig[g].as<float>(), st));
+    if (init) {
+      CK(cudaMalloc(&sinit[g].p, sizeof(float) * n * Q));
+      CK(launch_gather_rows(init, dr, n, Q, sinit[g].as<float>(), st));
+    }
+    prism_volume& pv = vols[g];
+    pv = *vol;
+    pv.nz = z1s[s] - z0s[s];
+    pv.mem = PRISM_MEM_DEVICE;
+    pv.mask = sub[s].data();
+    pv.signal = ssig[g].as<float>();
+    pv.init = init ? sinit[g].as<float>() : nullptr;
+  }
+  CK(cudaStreamSynchronize(st));
+  prism_handle* h = nullptr;
+  RC(prism_fit_init(vols.data(), G, &o, stream, &h));
+  CK(cudaStreamSynchronize(st));
+  h->slabbed = true;
+  h->st_src0 = std::move(src0);
+  h->st_src1 = std::move(src1);
+  h->st_w1 = std::move(w1);
+  *out = h;
+  return PRISM_OK;
+}
+
+extern "C" int prism_stitch_slabs(prism_handle* h, float* s0, float* fracs, float* fin, float* dirs, int32_t mem,
+                                  void* stream) {
+  if (!h) return fail(PRISM_E_INVALID_ARG, "handle is NULL");
+  if (!h->slabbed) return fail(PRISM_E_STATE, "the handle was not made by prism_fit_init_slabs");
+  if (mem != PRISM_MEM_HOST && mem != PRISM_MEM_DEVICE) return fail(PRISM_E_INVALID_ARG, "mem must be HOST or DEVICE");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t n = static_cast<int64_t>(h->st_src0.size());
+  const int K = h->K;
+  DevTmp d0, d1, dw, out;
+  CK(cudaMalloc(&d0.p, sizeof(int64_t) * n));
+  CK(cudaMalloc(&d1.p, sizeof(int64_t) * n));
+  CK(cudaMalloc(&dw.p, sizeof(float) * n));
+  CK(cudaMemcpyAsync(d0.p, h->st_src0.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d1.p, h->st_src1.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dw.p, h->st_w1.data(), sizeof(float) * n, cudaMemcpyHostToDevice, st));
+  const size_t ns = n, nf = n * (K + 3), nd = n * K * 3;
+  float *o_s0 = s0, *o_fr = fracs, *o_fin = fin, *o_d = dirs;
+  if (mem == PRISM_MEM_HOST) {
+    CK(cudaMalloc(&out.p, sizeof(float) * (2 * ns + nf + nd)));
+    float* b = out.as<float>();
+    o_s0 = s0 ? b : nullptr;
+    o_fin = fin ? b + ns : nullptr;
+    o_fr = fracs ? b + 2 * ns : nullptr;
+    o_d = dirs ? b + 2 * ns + nf : nullptr;
+  }
+  CK(h->ks->stitch(h->ia, h->d_slot_of_vox, n, d0.as<int64_t>(), d1.as<int64_t>(), dw.as<float>(), o_s0, o_fr,
+                   o_fin, o_d, st));
+  if (mem == PRISM_MEM_HOST) {
+    if (s0) CK(cudaMemcpyAsync(s0, o_s0, sizeof(float) * ns, cudaMemcpyDeviceToHost, st));
+    if (fin) CK(cudaMemcpyAsync(fin, o_fin, sizeof(float) * ns, cudaMemcpyDeviceToHost, st));
+    if (fracs) CK(cudaMemcpyAsync(fracs, o_fr, sizeof(float) * nf, cudaMemcpyDeviceToHost, st));
+    if (dirs) CK(cudaMemcpyAsync(dirs, o_d, sizeof(float) * nd, cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaStreamSynchronize(st));
   return PRISM_OK;
 }
 

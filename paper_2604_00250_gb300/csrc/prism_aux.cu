@@ -120,6 +120,16 @@ __global__ void k_pair_table(const MeasRow* rows, int N, int NP, MeasPair* out) 
   out[pidx] = mp;
 }
 
+// Row gather: dst[i][:] = src[rows[i]][:] (slab volumes cut from a whole volume).
+__global__ void k_gather_rows(const float* __restrict__ src, const int64_t* __restrict__ rows, int64_t n, int len,
+                              float* __restrict__ dst) {
+  const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= n * len) return;
+  const int64_t i = e / len;
+  const int c = static_cast<int>(e - i * len);
+  dst[e] = src[rows[i] * len + c];
+}
+
 __global__ void k_scatter_params(const float* __restrict__ in, const int32_t* __restrict__ slot_of_vox,
                                  int64_t V, int Q, int Vpad, float* __restrict__ theta) {
   const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -469,6 +479,12 @@ cudaError_t launch_pack(const IterArgs& a, const float* sig, const float* b0mean
   (void)bad;
   if (tile_end <= tile_begin) return cudaSuccess;
   k_pack<<<tile_end - tile_begin, 256, 0, st>>>(a, sig, b0mean, vox_of_slot, order, vox0, tile_begin, N, ypack);
+  return cudaGetLastError();
+}
+cudaError_t launch_gather_rows(const float* src, const int64_t* rows, int64_t n, int len, float* dst,
+                               cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_gather_rows<<<nblk(n * len, 256), 256, 0, st>>>(src, rows, n, len, dst);
   return cudaGetLastError();
 }
 cudaError_t launch_table(const float* bvals, const float* bvecs, int N, MeasRow* rows, cudaStream_t st) {

@@ -1020,6 +1020,103 @@ __global__ void k_fibers(const IterArgs a, const int32_t* __restrict__ slot_of_v
   }
 }
 
+// Slab stitching (Sec. 3 "Configuration": overlapping slabs stitched by weighted averaging;
+// reading R29). Output voxel v takes the estimate at handle voxel src0[v] and, where two slabs
+// overlap, blends in the one at src1[v] with weight w1[v] (src0's weight is 1 - w1). The
+// later slab's fibers are matched to the earlier slab's by the permutation maximising
+// sum_k |d0_k . d1_pi(k)| (FP64 dot products, first maximum in lexicographic order), each
+// matched direction is flipped into the same hemisphere, then S0, fractions, f_intra and the
+// directions are averaged and the directions renormalised.
+template <int K>
+__global__ void k_stitch(const IterArgs a, const int32_t* __restrict__ slot_of_vox, int64_t n_out,
+                         const int64_t* __restrict__ src0, const int64_t* __restrict__ src1,
+                         const float* __restrict__ w1, float* __restrict__ s0, float* __restrict__ fracs,
+                         float* __restrict__ fin, float* __restrict__ dirs) {
+  const int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (v >= n_out) return;
+  float th[4 * K + 5];
+  Vox<K> A;
+  load_theta<K>(a.theta, a.Vpad, slot_of_vox[src0[v]], true, th);
+  transform<K>(th, A);
+  float S = A.S0, fi = A.fin, f[K + 3], d[K][3];
+#pragma unroll
+  for (int i = 0; i < K + 3; ++i) f[i] = A.f[i];
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) d[k][c] = A.d[k][c];
+  const int64_t b = src1[v];
+  if (b >= 0) {
+    Vox<K> B;
+    load_theta<K>(a.theta, a.Vpad, slot_of_vox[b], true, th);
+    transform<K>(th, B);
+    double ad[K][K];
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+#pragma unroll
+      for (int j = 0; j < K; ++j)
+        ad[i][j] = fabs(static_cast<double>(A.d[i][0]) * B.d[j][0] + static_cast<double>(A.d[i][1]) * B.d[j][1] +
+                        static_cast<double>(A.d[i][2]) * B.d[j][2]);
+    // lexicographic permutations of 0..K-1 (next-permutation), first strict maximum kept
+    int p[K], bp[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) p[k] = bp[k] = k;
+    double best = -1.0;
+    for (;;) {
+      double sum = 0.0;
+      for (int k = 0; k < K; ++k) sum += ad[k][p[k]];
+      if (sum > best) {
+        best = sum;
+        for (int k = 0; k < K; ++k) bp[k] = p[k];
+      }
+      int i = K - 2;
+      while (i >= 0 && p[i] > p[i + 1]) --i;
+      if (i < 0) break;
+      int j = K - 1;
+      while (p[j] < p[i]) --j;
+      int t = p[i];
+      p[i] = p[j];
+      p[j] = t;
+      for (int l = i + 1, r = K - 1; l < r; ++l, --r) {
+        t = p[l];
+        p[l] = p[r];
+        p[r] = t;
+      }
+    }
+    const float wb = w1[v], wa = 1.f - wb;
+    S = wa * A.S0 + wb * B.S0;
+    fi = wa * A.fin + wb * B.fin;
+    f[0] = wa * A.f[0] + wb * B.f[0];
+    f[1] = wa * A.f[1] + wb * B.f[1];
+    f[K + 2] = wa * A.f[K + 2] + wb * B.f[K + 2];
+    for (int k = 0; k < K; ++k) {
+      const int m = bp[k];
+      const float dot = A.d[k][0] * B.d[m][0] + A.d[k][1] * B.d[m][1] + A.d[k][2] * B.d[m][2];
+      const float sg = (dot >= 0.f) ? wb : -wb;
+      f[2 + k] = wa * A.f[2 + k] + wb * B.f[2 + m];
+      float n2 = 0.f;
+      for (int c = 0; c < 3; ++c) {
+        d[k][c] = wa * A.d[k][c] + sg * B.d[m][c];
+        n2 += d[k][c] * d[k][c];
+      }
+      const float inv = rsqrtf(fmaxf(n2, kNormEps2));
+      for (int c = 0; c < 3; ++c) d[k][c] *= inv;
+    }
+  }
+  if (s0) s0[v] = S;
+  if (fin) fin[v] = fi;
+  if (fracs) {
+#pragma unroll
+    for (int i = 0; i < K + 3; ++i) fracs[v * (K + 3) + i] = f[i];
+  }
+  if (dirs) {
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) dirs[(v * K + k) * 3 + c] = d[k][c];
+  }
+}
+
 // Synthesis + calibration: y_hat for every (voxel, measurement) of the tile range.
 template <int K, int TPV, bool CAL>
 __global__ void __launch_bounds__(256) k_synth(const IterArgs a, const PlainArgs pa) {

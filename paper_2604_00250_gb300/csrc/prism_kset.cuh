@@ -137,13 +137,19 @@ cudaError_t l_fibers(const IterArgs& a, const int32_t* sov, int64_t V, float rel
   k_fibers<kK><<<nblocks(V, 128), 128, 0, st>>>(a, sov, V, rel, dirs, fracs, peaks);
   return cudaGetLastError();
 }
+cudaError_t l_stitch(const IterArgs& a, const int32_t* sov, int64_t n_out, const int64_t* src0, const int64_t* src1,
+                     const float* w1, float* s0, float* fracs, float* fin, float* dirs, cudaStream_t st) {
+  if (n_out <= 0) return cudaSuccess;
+  k_stitch<kK><<<nblocks(n_out, 128), 128, 0, st>>>(a, sov, n_out, src0, src1, w1, s0, fracs, fin, dirs);
+  return cudaGetLastError();
+}
 
 }  // namespace
 
 #define PRISM_CAT2(a, b) a##b
 #define PRISM_CAT(a, b) PRISM_CAT2(a, b)
 const KernelSet& PRISM_CAT(kernels_k, PRISM_K)() {
-  static const KernelSet ks = {l_fused, l_fused_occupancy, l_transform, l_synth, l_adjoint, l_prior_prep, l_prior, l_fibers};
+  static const KernelSet ks = {l_fused, l_fused_occupancy, l_transform, l_synth, l_adjoint, l_prior_prep, l_prior, l_fibers, l_stitch};
   return ks;
 }
 

@@ -20,6 +20,9 @@ struct KernelSet {
   cudaError_t (*prior)(const IterArgs& a, const PlainArgs& p, cudaStream_t st);
   cudaError_t (*fibers)(const IterArgs& a, const int32_t* slot_of_vox, int64_t V, float rel, float* dirs,
                         float* fracs, uint8_t* peaks, cudaStream_t st);
+  cudaError_t (*stitch)(const IterArgs& a, const int32_t* slot_of_vox, int64_t n_out, const int64_t* src0,
+                        const int64_t* src1, const float* w1, float* s0, float* fracs, float* fin, float* dirs,
+                        cudaStream_t st);
 };
 
 const KernelSet& kernels_for_k(int K);
@@ -59,6 +62,8 @@ cudaError_t launch_sigma_init(const double* part, int nblocks, int64_t V, int nb
 cudaError_t launch_pack(const IterArgs& a, const float* sig, const float* b0mean, const int32_t* vox_of_slot,
                         const int32_t* order, int64_t vox0, int tile_begin, int tile_end, int N, float* ypack,
                         int* bad, cudaStream_t st);
+cudaError_t launch_gather_rows(const float* src, const int64_t* rows, int64_t n, int len, float* dst,
+                               cudaStream_t st);
 cudaError_t launch_table(const float* bvals, const float* bvecs, int N, MeasRow* rows, cudaStream_t st);
 cudaError_t launch_pair_table(const MeasRow* rows, int N, MeasPair* out, cudaStream_t st);
 cudaError_t launch_scatter_params(const float* in, const int32_t* slot_of_vox, int64_t V, int Q, int Vpad,
