@@ -321,6 +321,41 @@ def run_ours(args):
     return 0
 
 
+# Crossing-fiber benchmark configuration (Sec. 3 "Configuration": K = 2, MSE and NLL with
+# learned sigma, direction repulsion only, no spatial priors); 300 Adam iterations.
+CROSS_OPTS = dict(K=2, lam_rep=0.01, lam_sparse=0.0, lam_sp=0.0, lam_dir=0.0, patch_dim=16)
+
+
+def run_crossing(args):
+    """Quality of the fit on the crossing-fiber benchmark layout (16 angles + single-fiber
+    controls, N = 193) at each SNR and both data terms: one JSON line per run with the
+    best-match angular error per angle, overall, recall and F1 (readings R20, R31)."""
+    import torch
+    import phantoms as P
+    import paper_2604_00250_gb300 as prism
+    from paper_2604_00250_gb300 import crossing
+    for snr in args.cross_snr:
+        vol = P.crossing_benchmark(snr=snr, seed=args.seed, n_per_case=args.cross_voxels)
+        for loss in ("mse", "nll"):
+            f = prism.Fitter(vol, prism.options(loss=loss, **CROSS_OPTS))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            f.step(args.cross_iters)
+            e1.record()
+            f.sync()
+            d, _, pk = f.fibers(0.15)
+            per, overall, rec, prec, f1 = crossing.score(d, pk, vol.gt["dirs"], vol.gt["ffib"], vol.gt["case"])
+            line = {"workload": "crossing_benchmark_N193_K2", "snr": snr, "loss": loss, "voxels": f.n_vox,
+                    "iterations": args.cross_iters, "fit_ms": e0.elapsed_time(e1),
+                    "single_fiber_deg": per[0],
+                    "per_angle_deg": {str(a): per[i + 1] for i, a in enumerate(P.BENCH_ANGLES)},
+                    "overall_deg": overall, "recall": rec, "precision": prec, "f1": f1,
+                    "final_loss": float(f.loss()[0])}
+            print(json.dumps(line), flush=True)
+            f.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -337,7 +372,14 @@ def main():
     ap.add_argument("--no-unfused", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="brain", choices=["brain", "crossing"],
+                    help="crossing: fit quality on the crossing-fiber benchmark layout instead of timing")
+    ap.add_argument("--cross-snr", type=float, nargs="+", default=[10.0, 30.0, 50.0])
+    ap.add_argument("--cross-voxels", type=int, default=200, help="voxels per angle (and single-fiber controls)")
+    ap.add_argument("--cross-iters", type=int, default=300)
     args = ap.parse_args()
+    if args.workload == "crossing":
+        return run_crossing(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -75,3 +75,43 @@ def best_match_error(theta, gt_dirs, gt_ffib, K, rel_thresh=0.15, match_deg=20.0
     precision = hit / max(hit + fp, 1)
     f1 = 2 * precision * recall / max(precision + recall, 1e-12)
     return float(np.mean(errs)) if errs else float("nan"), recall, f1
+
+
+def crossing_scores(dirs, peaks, gt_dirs, gt_ffib, case, match_deg=20.0):
+    """Crossing-benchmark scores (Sec. 3 "Tracking & metrics"; reading R31).
+
+    dirs [V, K, 3] fitted unit directions, peaks [V, K] bool (R20), gt_dirs [V, F, 3],
+    gt_ffib [V, F] (a ground-truth fiber exists where > 0), case [V] integer label.
+    Best-match angular error: every ground-truth fiber is matched to its closest predicted
+    peak (several may share one); errors are pooled over ground-truth fibers, per case and
+    overall. Detection: predicted peaks and ground-truth fibers are paired one to one,
+    greedily by increasing angle, pairs within match_deg counting as true positives;
+    recall = TP / ground-truth fibers, precision = TP / predicted peaks, F1 their harmonic
+    mean. Returns (per_case {label: mean error}, overall error, recall, precision, F1).
+    """
+    per = {}
+    errs_all = []
+    tp = n_gt = n_pred = 0
+    for v in range(dirs.shape[0]):
+        pred = [dirs[v, k] for k in range(dirs.shape[1]) if peaks[v, k]]
+        gts = [gt_dirs[v, j] for j in range(gt_dirs.shape[1]) if gt_ffib[v, j] > 0]
+        n_gt += len(gts)
+        n_pred += len(pred)
+        for g in gts:
+            e = min(float(angle_deg(p, g)) for p in pred)
+            per.setdefault(int(case[v]), []).append(e)
+            errs_all.append(e)
+        pairs = sorted((float(angle_deg(p, g)), i, j) for i, p in enumerate(pred) for j, g in enumerate(gts))
+        used_p, used_g = set(), set()
+        for a, i, j in pairs:
+            if a > match_deg:
+                break
+            if i in used_p or j in used_g:
+                continue
+            used_p.add(i)
+            used_g.add(j)
+            tp += 1
+    recall = tp / max(n_gt, 1)
+    precision = tp / max(n_pred, 1)
+    f1 = 2 * precision * recall / max(precision + recall, 1e-12)
+    return ({c: float(np.mean(v)) for c, v in sorted(per.items())}, float(np.mean(errs_all)), recall, precision, f1)

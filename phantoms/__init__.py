@@ -18,14 +18,14 @@ Layouts (the library's input format):
   bvals  float32 [N]      s/mm^2
   bvecs  float32 [N, 3]   unit vectors (zero rows for b = 0)
 """
-from .schemes import (electrostatic_directions, make_scheme, scheme_96, scheme_288,
+from .schemes import (electrostatic_directions, make_scheme, scheme_96, scheme_193, scheme_288,
                       scheme_360)
-from .volumes import (Volume, crossing_patch, crossing_sweep, bundle_phantom,
+from .volumes import (BENCH_ANGLES, Volume, crossing_benchmark, crossing_patch, crossing_sweep, bundle_phantom,
                       brain_phantom, multi_volume_batch, random_volume, default_init,
                       n_params)
 
 __all__ = [
-    "electrostatic_directions", "make_scheme", "scheme_96", "scheme_288", "scheme_360",
-    "Volume", "crossing_patch", "crossing_sweep", "bundle_phantom", "brain_phantom",
+    "electrostatic_directions", "make_scheme", "scheme_96", "scheme_193", "scheme_288", "scheme_360",
+    "BENCH_ANGLES", "crossing_benchmark", "Volume", "crossing_patch", "crossing_sweep", "bundle_phantom", "brain_phantom",
     "multi_volume_batch", "random_volume", "default_init", "n_params",
 ]

@@ -71,3 +71,9 @@ def scheme_288(seed=0):
 def scheme_360(seed=0):
     """20 b=0 + 113/113/114 directions at b = 650/1500/4000 (N = 360)."""
     return make_scheme(20, [(650, 113), (1500, 113), (4000, 114)], seed)
+
+
+def scheme_193(seed=0):
+    """1 b=0 + 64 directions at each of b = 1000/2000/3000 (N = 193, the crossing-fiber
+    benchmark's acquisition, Sec. 3 "Datasets")."""
+    return make_scheme(1, [(1000, 64), (2000, 64), (3000, 64)], seed)

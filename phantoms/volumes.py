@@ -11,7 +11,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .schemes import scheme_96, scheme_288, scheme_360
+from .schemes import scheme_96, scheme_193, scheme_288, scheme_360
 
 D_ISO = (3.0e-3, 0.9e-3, 0.2e-3)  # CSF, GM, restricted (mm^2/s)
 
@@ -149,6 +149,44 @@ def crossing_patch(seed=0, edge=8, snr=30.0, device="cpu"):
     gt = _crossing_voxels(V, rng.uniform(20.0, 90.0, V), rng)
     mask = np.ones((edge, edge, edge), dtype=np.uint8)
     return _finish(mask, scheme_96(seed), gt, snr, rng, device)
+
+
+BENCH_ANGLES = tuple(range(15, 91, 5))      # 16 crossing angles, degrees
+
+
+def crossing_benchmark(snr=30.0, seed=0, n_per_case=200, device="cpu"):
+    """The crossing-fiber benchmark's layout (Sec. 3 "Datasets"): 16 crossing angles
+    15, 20, ..., 90 deg and single-fiber controls, n_per_case voxels each (3400 at 200),
+    N = 193 (1 b=0 + 64 directions x 1000/2000/3000), Rician noise at the given SNR.
+
+    Each fiber is an axially symmetric tensor with eigenvalues (1.7, 0.3, 0.3) x 1e-3 mm^2/s
+    (the fit model's 0.4 perpendicular diffusivity is deliberately different, Sec. 4), equal
+    fractions for the two fibers of a crossing, no isotropic compartment, S0 = 1. The mask is
+    [17, n_per_case, 1]: row 0 holds the single-fiber controls, row i the crossings at
+    BENCH_ANGLES[i - 1]. gt["case"] is that row per voxel, gt["angle"] the crossing angle
+    (0 for the controls).
+    """
+    rng = np.random.default_rng([seed, 7])
+    n = int(n_per_case)
+    cases = np.repeat(np.arange(len(BENCH_ANGLES) + 1), n)
+    V = cases.shape[0]
+    angles = np.concatenate([np.zeros(n)] + [np.full(n, float(a)) for a in BENCH_ANGLES])
+    d1 = _unit(rng.standard_normal((V, 3)))
+    d2 = _rotate_about(d1, np.deg2rad(np.maximum(angles, 1.0)), rng)
+    ffib = np.where(cases[:, None] == 0, np.array([[1.0, 0.0]]), np.array([[0.5, 0.5]]))
+    gt = dict(
+        dirs=np.stack([d1, d2], axis=1),
+        ffib=ffib,
+        fiso=np.zeros((V, 3)),
+        dpar=np.full(V, 1.7e-3),
+        dperp=np.full(V, 0.3e-3),
+        fin=np.zeros(V),
+        s0=np.ones(V),
+        angle=angles,
+        case=cases,
+    )
+    mask = np.ones((len(BENCH_ANGLES) + 1, n, 1), dtype=np.uint8)
+    return _finish(mask, scheme_193(seed), gt, snr, rng, device)
 
 
 def crossing_sweep(seed=0, edge=10, n_angles=16, snr=30.0, device="cpu"):

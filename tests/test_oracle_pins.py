@@ -538,3 +538,35 @@ def test_ordering_kink_has_zero_derivative():
     _, parts = O.objective(ov, th, O.group_init(ov))
     (g,) = torch.autograd.grad(parts["order"], th)
     assert float(parts["order"]) == 0.0 and float(g.abs().max()) == 0.0
+
+
+def test_crossing_scores_hand_cases():
+    """Crossing-benchmark scoring (R31): a single peak on the bisector of a 30 deg crossing
+    has best-match error 15 deg for both fibers and detects one of the two; an exact fit
+    scores 0 deg and F1 = 1; a spurious third peak lowers precision only."""
+    from oracle import metrics as M
+    a = np.deg2rad(30.0)
+    g1 = np.array([1.0, 0.0, 0.0])
+    g2 = np.array([np.cos(a), np.sin(a), 0.0])
+    bis = (g1 + g2) / np.linalg.norm(g1 + g2)
+    z = np.array([0.0, 0.0, 1.0])
+    gt = np.stack([np.stack([g1, g2]), np.stack([g1, g2])])
+    ff = np.array([[0.5, 0.5], [0.5, 0.5]])
+    case = np.array([3, 5])
+    # voxel 0: one peak on the bisector (second fiber below threshold); voxel 1: exact, negated
+    dirs = np.stack([np.stack([bis, z, z]), np.stack([-g2, g1, z])])
+    peaks = np.array([[True, False, False], [True, True, False]])
+    per, overall, rec, prec, f1 = M.crossing_scores(dirs, peaks, gt, ff, case)
+    assert abs(per[3] - 15.0) < 1e-9 and abs(per[5]) < 1e-6
+    assert abs(overall - 7.5) < 1e-9
+    assert rec == 3 / 4 and prec == 1.0
+    assert abs(f1 - 2 * 0.75 / 1.75) < 1e-12
+    # a spurious orthogonal peak in voxel 1
+    peaks2 = peaks.copy()
+    peaks2[1, 2] = True
+    _, overall2, rec2, prec2, _ = M.crossing_scores(dirs, peaks2, gt, ff, case)
+    assert overall2 == overall and rec2 == rec and prec2 == 3 / 4
+    # single-fiber ground truth (second gt fraction 0) ignores the second gt direction
+    ff1 = np.array([[1.0, 0.0], [1.0, 0.0]])
+    per1, _, rec1, _, _ = M.crossing_scores(dirs, peaks, gt, ff1, np.array([0, 0]))
+    assert abs(per1[0] - 7.5) < 1e-9 and rec1 == 1.0
