@@ -717,7 +717,6 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_iter_fused(const IterArgs 
   };
 
   while (t < a.ntiles) {
-    // next tile: round-robin while static tiles remain (no atomic, no barrier), then the queue
     if (tid == 0) s_next = atomicAdd(a.queue, 1);
     __syncthreads();
     const int t_next = s_next;
@@ -1292,11 +1291,29 @@ __global__ void k_prior_prep(const IterArgs a, int tile_begin, int tile_end) {
     float sum[NF];
 #pragma unroll
     for (int c = 0; c < NF; ++c) sum[c] = 0.f;
-    for (int e = 0; e < a.n_nbr; ++e) {
-      const int x = a.nbr[static_cast<size_t>(e) * Vp + slot];
-      if (x < 0) continue;
+    if (a.n_nbr == 6) {
+      // every index first, then every neighbour's fractions (a missing neighbour reads the
+      // voxel's own row and adds nothing), so that the gathers are in flight together
+      int xs[6];
 #pragma unroll
-      for (int c = 0; c < NF; ++c) sum[c] += xf[static_cast<size_t>(c) * Vp + x];
+      for (int e = 0; e < 6; ++e) xs[e] = a.nbr[static_cast<size_t>(e) * Vp + slot];
+#pragma unroll
+      for (int e = 0; e < 6; ++e) {
+        const bool ok = xs[e] >= 0;
+        const int x = ok ? xs[e] : slot;
+#pragma unroll
+        for (int c = 0; c < NF; ++c) {
+          const float v = xf[static_cast<size_t>(c) * Vp + x];
+          sum[c] += ok ? v : 0.f;
+        }
+      }
+    } else {
+      for (int e = 0; e < a.n_nbr; ++e) {
+        const int x = a.nbr[static_cast<size_t>(e) * Vp + slot];
+        if (x < 0) continue;
+#pragma unroll
+        for (int c = 0; c < NF; ++c) sum[c] += xf[static_cast<size_t>(c) * Vp + x];
+      }
     }
     const float inv_n = 1.f / static_cast<float>(ncnt);
 #pragma unroll
