@@ -40,6 +40,10 @@ FLOPS_PER_PAIR = 17 + 28 * K_FIB
 # Pairs of b = 0 measurements (the kernel's table starts with them) need no fiber terms:
 # r = y - S0 sum(f) and r^2 (two multiply-adds) and the running sum of r (one add).
 FLOPS_PER_B0_PAIR = 5
+# DRAM bytes per voxel-iteration of the fused kernel (read + write), from an ncu capture of
+# this kernel version on the scaled brain; traffic grows in proportion to the voxels
+# (profiles/k_iter_fused_hcp_brain_dram_traffic.md). Must return to None when the kernel changes.
+TRAFFIC_BYTES_PER_VOXEL_ITER = 1860.0
 # FP32 peak: 152 SMs x 128 lanes x 2 flops x 2070 MHz (maximum SM clock).
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
@@ -307,7 +311,9 @@ def run_ours(args):
                 "config": cfg_dict(V, {"timing": "CUDA events, graph replay, max over ranks",
                                        "brain_scale": args.brain_scale}),
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
-                             "frac": achieved / PEAK_FP32_TFLOPS, "traffic": None,
+                             "frac": achieved / PEAK_FP32_TFLOPS,
+                             "traffic": (V * TRAFFIC_BYTES_PER_VOXEL_ITER if TRAFFIC_BYTES_PER_VOXEL_ITER else None),
+                             "traffic_unit": "bytes per launch (ncu dram read + write, scaled capture)",
                              "kernel": "k_iter_fused", "kernel_ms": fused_ms,
                              "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
                 "unfused": unfused,
