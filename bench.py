@@ -35,14 +35,14 @@ PRIORS = dict(lam_rep=0.01, lam_sparse=0.02, lam_sp=0.01, lam_dir=0.005)
 
 # FP32 floating-point operations per (voxel, measurement) pair of the fused kernel's hot
 # loop on this workload (packed two-measurement path: MSE, no calibration), fused
-# multiply-add = 2: 17 per measurement + 28 per fiber (itemised in the design doc).
+# multiply-add = 2: 17 per measurement + 28 per fiber.
 FLOPS_PER_PAIR = 17 + 28 * K_FIB
 # Pairs of b = 0 measurements (the kernel's table starts with them) need no fiber terms:
 # r = y - S0 sum(f) and r^2 (two multiply-adds) and the running sum of r (one add).
 FLOPS_PER_B0_PAIR = 5
 # DRAM bytes per voxel-iteration of the fused kernel (read + write), from an ncu capture of
-# this kernel version on the scaled brain; traffic grows in proportion to the voxels
-# (profiles/k_iter_fused_hcp_brain_dram_traffic.md). Must return to None when the kernel changes.
+# this kernel version on the scaled brain (212,900 voxels: 396.0 MB per launch); traffic grows
+# in proportion to the voxels. Must return to None when the kernel changes.
 TRAFFIC_BYTES_PER_VOXEL_ITER = 1860.0
 # FP32 peak: 152 SMs x 128 lanes x 2 flops x 2070 MHz (maximum SM clock).
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12

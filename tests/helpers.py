@@ -7,7 +7,7 @@ import torch
 import phantoms as P
 from oracle import prism_oracle as O
 
-# Tolerances (BASELINE contract, restated in the design doc): signal and objective relative
+# Tolerances: signal and objective relative
 # error <= 1e-5 (signal relative to max(|y_hat|, 1e-3)); gradient normwise relative error
 # <= 1e-4 per parameter block.
 TOL_SIGNAL = 1e-5
