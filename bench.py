@@ -332,6 +332,48 @@ def run_ours(args):
 CROSS_OPTS = dict(K=2, lam_rep=0.01, lam_sparse=0.0, lam_sp=0.0, lam_dir=0.0, patch_dim=16)
 
 
+def run_calibrated(args):
+    """Speed of the calibrated Rician-NLL configurations (one JSON line each, not the headline):
+    'bundle' = the 64^3 bundle phantom (N = 360, bias field and per-measurement affine, SNR 20);
+    'multi' = the batch of 12 volumes of edge 32..128 (schemes of 96/288/360 measurements,
+    about 4 M voxels), both with K = 3, NLL with learned sigma, full calibration and the
+    neighbour priors, in 16^3 patches. Reports voxel-iterations/s of graph-replayed fused
+    iterations, the per-kernel times and the device memory the fit holds."""
+    import types
+    import torch
+    import phantoms as P
+    import paper_2604_00250_gb300 as prism
+    vols = ([P.bundle_phantom(args.seed, device="cuda")] if args.workload == "bundle"
+            else P.multi_volume_batch(args.seed, device="cuda"))
+    gv = [types.SimpleNamespace(mask=v.mask, signal=torch.as_tensor(v.signal, device="cuda"), bvals=v.bvals,
+                                bvecs=v.bvecs, init=None) for v in vols]
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    opts = dict(K=3, loss="nll", calibration=True, lam_sp=0.01, lam_dir=0.005, patch_dim=16)
+    f = prism.Fitter(gv, prism.options(**opts))
+    torch.cuda.synchronize()
+    held = free0 - torch.cuda.mem_get_info()[0]
+    f.step(args.warmup)
+    f.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = min(args.steps, 500)
+    e0.record()
+    f.step(steps)
+    e1.record()
+    f.sync()
+    ms = e0.elapsed_time(e1) / steps
+    prof = f.profile(20)
+    line = {"workload": ("bundle_64cubed_N360_nll_calibrated" if args.workload == "bundle"
+                         else "multi_volume_12_edges_32_to_128_N96_288_360_nll_calibrated"),
+            "voxels": f.n_vox, "volumes": f.n_groups, "value": f.n_vox / (ms / 1e3),
+            "unit": "voxel-iterations/s", "ms_per_step": ms, "steps": steps, "profile_ms": prof,
+            "signal_bytes": int(sum(v.signal.numel() * 4 for v in gv)), "fit_device_bytes": int(held),
+            "options": opts}
+    print(json.dumps(line), flush=True)
+    f.close()
+    return 0
+
+
 def run_crossing(args):
     """Quality of the fit on the crossing-fiber benchmark layout (16 angles + single-fiber
     controls, N = 193) at each SNR and both data terms: one JSON line per run with the
@@ -378,14 +420,17 @@ def main():
     ap.add_argument("--no-unfused", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="brain", choices=["brain", "crossing"],
-                    help="crossing: fit quality on the crossing-fiber benchmark layout instead of timing")
+    ap.add_argument("--workload", default="brain", choices=["brain", "crossing", "bundle", "multi"],
+                    help="crossing: fit quality on the crossing-fiber benchmark layout; bundle / multi: "
+                         "speed of the calibrated NLL configurations (not the headline)")
     ap.add_argument("--cross-snr", type=float, nargs="+", default=[10.0, 30.0, 50.0])
     ap.add_argument("--cross-voxels", type=int, default=200, help="voxels per angle (and single-fiber controls)")
     ap.add_argument("--cross-iters", type=int, default=300)
     args = ap.parse_args()
     if args.workload == "crossing":
         return run_crossing(args)
+    if args.workload in ("bundle", "multi"):
+        return run_calibrated(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -243,7 +243,7 @@ __device__ __forceinline__ void bessel_QL(float z, float& Q, float& L) {
       i0 = fmaf(i0, t, k_bessel_s0[k]);
       i1 = fmaf(i1, t, k_bessel_s1[k]);
     }
-    Q = 1.f - 0.5f * z * i1 / i0;
+    Q = 1.f - 0.5f * z * i1 * rcpf_(i0);   // i0 >= 1
     if (WANT_L) L = lg2f_(i0) * kLn2 - z;
   } else {
     const float x = PRISM_BESSEL_ZS * rcpf_(z);
@@ -310,6 +310,34 @@ __device__ __forceinline__ float warp_sum_range(float x) {
   for (int o = FIRST; o <= LAST; o <<= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
   return x;
 }
+// Reduce-scatter over a warp: every lane holds G values v[0..G-1] (G = 2, 4 or 8); on return
+// each lane holds the warp-wide sum of v[m] for m = its bits (4 .. 5 - log2 G) read as a binary
+// number, i.e. m = lane >> (5 - log2 G). Halving exchanges (xor 16, 8, ...) move half of the
+// remaining values per stage, then an all-reduce over the low lane bits: log2 G + (5 - log2 G)
+// shuffles of G - 1 + (5 - log2 G) values in all, instead of 5 G for G separate all-reduces.
+template <int G>
+__device__ __forceinline__ float warp_scatter_sum(float (&v)[G]) {
+  static_assert(G == 2 || G == 4 || G == 8, "G must be 2, 4 or 8");
+  constexpr int LG = (G == 2) ? 1 : (G == 4) ? 2 : 3;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int st = 0; st < LG; ++st) {
+    const int o = 16 >> st;
+    const int half = G >> (st + 1);
+    const bool hi = (lane & o) != 0;
+#pragma unroll
+    for (int k = 0; k < half; ++k) {
+      const float send = hi ? v[k] : v[k + half];
+      const float keep = hi ? v[k + half] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  float x = v[0];
+#pragma unroll
+  for (int o = 16 >> LG; o >= 1; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
 __device__ __forceinline__ double warp_sum_d(double x) {
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) x += __shfl_xor_sync(0xffffffffu, x, o);

@@ -582,6 +582,7 @@ __device__ __forceinline__ void block_reduce3(double v0, double v1, double v2, d
 // The measurement table and the bias grid arrive by bulk copy when the group changes.
 // ===========================================================================
 constexpr int kChunk = 32;    // measurements per ring stage
+constexpr int kCalG = 4;      // measurements per warp reduce-scatter of the calibration partials
 constexpr int kStages = 2;    // ring depth per warp
 constexpr int kFusedThreads = 128;
 
@@ -846,6 +847,30 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_iter_fused(const IterArgs 
           const int nl = i * TPV + js;
           float rr, u;
           pair<K, LOSS, CAL, false>(P, ffin, fomf, tab[nl], yc[(nl >> 1) * (2 * VW) + (nl & 1)], B, inv_s2, 0.f, A, rr, u);
+        }
+      } else if (CAL && TPV == 1) {
+        // per-measurement alpha / beta partials summed over the warp's 32 voxels, kCalG
+        // measurements at a time by one reduce-scatter (lane L ends with measurement
+        // L / (32 / kCalG) of the group; the first lane of each run of 32 / kCalG stores it)
+        constexpr int G = kCalG;
+        for (int i0 = 0; i0 < kChunk; i0 += G) {
+          float uu[G], rv[G];
+#pragma unroll
+          for (int gq = 0; gq < G; ++gq) {
+            const int nl = i0 + gq;
+            const bool ok = act && (nl < cnt);
+            float rr = 0.f, u = 0.f;
+            if (ok) pair<K, LOSS, CAL, false>(P, ffin, fomf, tab[nl], yc[(nl >> 1) * (2 * VW) + (nl & 1)], B, inv_s2, 0.f, A, rr, u);
+            uu[gq] = ok ? u : 0.f;
+            rv[gq] = ok ? rr : 0.f;
+          }
+          const float su = warp_scatter_sum<G>(uu);
+          const float sr = warp_scatter_sum<G>(rv);
+          const int m = lane >> (G == 8 ? 2 : G == 4 ? 3 : 4);
+          if ((lane & (32 / G - 1)) == 0 && i0 + m < cnt) {
+            s_ab[(warp * 2) * a.Nmax + j * kChunk + i0 + m] = su;
+            s_ab[(warp * 2 + 1) * a.Nmax + j * kChunk + i0 + m] = sr;
+          }
         }
       } else {
 #pragma unroll 4
