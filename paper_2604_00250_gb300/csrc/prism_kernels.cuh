@@ -406,6 +406,7 @@ struct AccP {
   float2 gcsf, ggm, gres, l1;
   float2 gwa[K], gwb[K];
   float2 gd[K][3];
+  float l2, l3;   // Rician NLL only: sum y |y_hat| Q, sum L
 };
 
 __device__ __forceinline__ float2 dup2(float x) { return make_float2(x, x); }
@@ -435,11 +436,31 @@ __device__ __forceinline__ void voxp_init(const Vox<K>& P, VoxP<K>& D, AccP<K>& 
     A.gwa[k] = A.gwb[k] = z;
     A.gd[k][0] = A.gd[k][1] = A.gd[k][2] = z;
   }
+  A.l2 = A.l3 = 0.f;
+}
+
+// Rician NLL terms of one measurement (Eq. 9) for the packed path: adds (y - |y_hat|)^2 to l1,
+// y |y_hat| Q(z) to l2 and L(z) to l3, and returns dL/dy_hat unscaled (y_hat - y R(z)); a
+// lane with m = 0 (padding) adds nothing.
+__device__ __forceinline__ float nll_lane(float yh, float yv, float inv_s2, float m, float& l1, float& l2,
+                                          float& l3) {
+  const float ay = fabsf(yh);
+  const float sy = (yh >= 0.f) ? yv : -yv;
+  float Qz, Lz;
+  bessel_QL<true>(yv * ay * inv_s2, Qz, Lz);
+  const float e = yv - ay;
+  l1 = fmaf(m * e, e, l1);
+  l2 = fmaf(m * yv * ay, Qz, l2);
+  l3 = fmaf(m, Lz, l3);
+  return m * fmaf(sy, Qz, yh - sy);
 }
 
 // One packed step over measurements (2p, 2p+1). With MASK, lanes whose msk is 0 add nothing.
-template <int K, bool MASK>
-__device__ __forceinline__ void step2(const VoxP<K>& D, const MeasPair& R, float2 y, float2 msk, AccP<K>& A) {
+// MSE: the data-term accumulators take r = y - y_hat. Rician NLL: they take -dL/dy_hat
+// (unscaled), the same sign convention, and l1..l3 collect the objective's sums.
+template <int K, bool MASK, int LOSS = kLossMSE>
+__device__ __forceinline__ void step2(const VoxP<K>& D, const MeasPair& R, float2 y, float2 msk, AccP<K>& A,
+                                      float inv_s2 = 0.f) {
   const float4 q0 = R.q[0], q1 = R.q[1], q2 = R.q[2], q3 = R.q[3], q4 = R.q[4], q5 = R.q[5];
   const float2 gx = lo2(q0), gy = hi2(q0), gz = lo2(q1), nkpar = hi2(q1);
   const float2 nkperp = lo2(q2), nkd = hi2(q2), ecsf = lo2(q3), egm = hi2(q3);
@@ -456,9 +477,16 @@ __device__ __forceinline__ void step2(const VoxP<K>& D, const MeasPair& R, float
     p[k] = ex2_2(__ffma2_rn(nkd, c2, nkperp));
     T = __ffma2_rn(D.ffin[k], e1[k], __ffma2_rn(D.fomf[k], p[k], T));
   }
-  float2 r = __ffma2_rn(D.nS0, T, y);   // y - y_hat
-  if (MASK) r = __fmul2_rn(r, msk);
-  A.l1 = __ffma2_rn(r, r, A.l1);
+  float2 r;
+  if constexpr (LOSS == kLossMSE) {
+    r = __ffma2_rn(D.nS0, T, y);   // y - y_hat
+    if (MASK) r = __fmul2_rn(r, msk);
+    A.l1 = __ffma2_rn(r, r, A.l1);
+  } else {
+    const float2 yh = __fmul2_rn(D.nS0, T);   // -y_hat
+    r.x = -nll_lane(-yh.x, y.x, inv_s2, MASK ? msk.x : 1.f, A.l1.x, A.l2, A.l3);
+    r.y = -nll_lane(-yh.y, y.y, inv_s2, MASK ? msk.y : 1.f, A.l1.y, A.l2, A.l3);
+  }
   A.gcsf = __ffma2_rn(r, ecsf, A.gcsf);
   A.ggm = __ffma2_rn(r, egm, A.ggm);
   A.gres = __ffma2_rn(r, eres, A.gres);
@@ -506,12 +534,16 @@ __device__ __forceinline__ void step2_b0(const VoxP<K>& D, const float2* __restr
 
 // Fold packed accumulators into the scalar ones (dJ/dS0 from the compartment sums:
 // sum_n q T = f_csf sum q E_csf + ... + sum_k (f_k f_in sum q e1 + f_k (1-f_in) sum q p)).
-template <int K>
+template <int K, int LOSS>
 __device__ __forceinline__ void accp_fold(const Vox<K>& P, const AccP<K>& B, Acc<K>& A) {
   A.gcsf = -(B.gcsf.x + B.gcsf.y);
   A.ggm = -(B.ggm.x + B.ggm.y);
   A.gres = -(B.gres.x + B.gres.y);
   A.l1 = B.l1.x + B.l1.y;
+  if constexpr (LOSS == kLossNLL) {
+    A.l2 = B.l2;
+    A.l3 = B.l3;
+  }
   float g = P.f[0] * A.gcsf + P.f[1] * A.ggm + P.f[K + 2] * A.gres;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -668,8 +700,8 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_iter_fused(const IterArgs 
   constexpr int NF = K + 3, Q = 4 * K + 5, XF = 4 * K + 3;
   constexpr int NW = kFusedThreads / 32;
   constexpr int VW = 32 / TPV;              // voxels per warp
-  constexpr bool PACKED = (TPV == 1) && (LOSS == kLossMSE) && !CAL;
-  constexpr bool HOIST = PACKED && K <= 3;
+  constexpr bool PACKED = (TPV == 1) && !CAL;
+  constexpr bool HOIST = PACKED && K <= 3 && LOSS == kLossMSE;
   static_assert(kChunk % TPV == 0, "chunk must split evenly across the voxel's lanes");
   extern __shared__ __align__(16) unsigned char smem[];
   const int Vp = a.Vpad;
@@ -822,16 +854,19 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_iter_fused(const IterArgs 
       if constexpr (PACKED) {
         const float2* __restrict__ yc2 = reinterpret_cast<const float2*>(ring + s * (kChunk * VW)) + lv;
         const MeasPair* __restrict__ tab2 = reinterpret_cast<const MeasPair*>(s_tab) + j * (kChunk / 2);
-        // leading pairs of b = 0 measurements (the group's table starts with them)
-        const int i0 = max(0, min(kChunk / 2, gr.nb0p - j * (kChunk / 2)));
+        // leading pairs of b = 0 measurements (the group's table starts with them); the NLL
+        // still needs the Bessel terms there, so it takes them as ordinary pairs
+        const int i0 = (LOSS == kLossMSE) ? max(0, min(kChunk / 2, gr.nb0p - j * (kChunk / 2))) : 0;
         if (act && cnt == kChunk && i0 == 0) {
 #pragma unroll 2
-          for (int i = 0; i < kChunk / 2; ++i) step2<K, false>(DP, tab2[i], yc2[i * VW], make_float2(1.f, 1.f), AP);
+          for (int i = 0; i < kChunk / 2; ++i)
+            step2<K, false, LOSS>(DP, tab2[i], yc2[i * VW], make_float2(1.f, 1.f), AP, inv_s2);
         } else if (act) {
           if (i0 > 0) step2_b0<K>(DP, yc2, VW, i0, AP);
 #pragma unroll 1
           for (int i = i0; i < (cnt + 1) / 2; ++i)
-            step2<K, true>(DP, tab2[i], yc2[i * VW], make_float2(1.f, (2 * i + 1 < cnt) ? 1.f : 0.f), AP);
+            step2<K, true, LOSS>(DP, tab2[i], yc2[i * VW], make_float2(1.f, (2 * i + 1 < cnt) ? 1.f : 0.f), AP,
+                                 inv_s2);
         }
         __syncwarp();
         ++g;
@@ -901,7 +936,7 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_iter_fused(const IterArgs 
     load_theta<K>(a.theta, Vp, slot, act, th);
     if constexpr (HOIST) load_moments<Q>(a, slot, writer, mq, vq);
     transform<K>(th, P);
-    if constexpr (PACKED) accp_fold<K>(P, AP, A);
+    if constexpr (PACKED) accp_fold<K, LOSS>(P, AP, A);
     acc_reduce_tpv<K, TPV>(A);
 
     // ---- data-term gradient and value
