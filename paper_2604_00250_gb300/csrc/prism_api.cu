@@ -316,6 +316,7 @@ void fill_args(prism_handle* h) {
   g.gv = h->d_gv;
   g.gparams = h->d_gparams;
   g.table = h->d_table;
+  g.table2 = h->d_table2;
   g.slot_of_grid = h->d_slot_of_grid;
   g.hist = h->d_hist;
   g.hist_len = kHistLen;

@@ -395,8 +395,14 @@ __global__ void __launch_bounds__(256) k_group_adam(const IterArgs a, const Grou
         if (i >= 4 && i < 4 + 2 * N4) {
           const int n = (i < 4 + N4) ? i - 4 : i - 4 - N4;
           MeasRow* row = g.table + gr.table_off + n;
-          if (i < 4 + N4) row->A = expf(xn);
-          else row->beta = xn;
+          float* pr = reinterpret_cast<float*>(g.table2 + gr.table2_off + n / 2) + (n & 1);
+          if (i < 4 + N4) {
+            row->A = expf(xn);
+            pr[2 * kPairFieldA] = row->A;
+          } else {
+            row->beta = xn;
+            pr[2 * kPairFieldBeta] = xn;
+          }
         }
       }
     }
@@ -429,6 +435,9 @@ __global__ void k_table_refresh(const GroupArgs g, const IterArgs a) {
     MeasRow* row = g.table + gr.table_off + n;
     row->A = gr.calib ? expf(g.gparams[gr.gp_off + 4 + n]) : 1.f;
     row->beta = gr.calib ? g.gparams[gr.gp_off + 4 + gr.N4 + n] : 0.f;
+    float* pr = reinterpret_cast<float*>(g.table2 + gr.table2_off + n / 2) + (n & 1);
+    pr[2 * kPairFieldA] = row->A;
+    pr[2 * kPairFieldBeta] = row->beta;
   }
 }
 

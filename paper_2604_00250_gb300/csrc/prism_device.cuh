@@ -42,6 +42,8 @@ struct __align__(16) MeasRow {
 struct __align__(16) MeasPair {
   float4 q[8];
 };
+// Field positions (MeasRow order) of e^alpha_n and beta_n in the paired table.
+constexpr int kPairFieldA = 11, kPairFieldBeta = 12;
 
 // A tile: up to TV voxels of one patch, processed by one CTA.
 struct Tile {

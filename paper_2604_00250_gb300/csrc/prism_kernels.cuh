@@ -407,6 +407,7 @@ struct AccP {
   float2 gwa[K], gwb[K];
   float2 gd[K][3];
   float l2, l3;   // Rician NLL only: sum y |y_hat| Q, sum L
+  float2 u;       // calibration only: sum q S (dJ/dU unscaled, negated)
 };
 
 __device__ __forceinline__ float2 dup2(float x) { return make_float2(x, x); }
@@ -437,6 +438,7 @@ __device__ __forceinline__ void voxp_init(const Vox<K>& P, VoxP<K>& D, AccP<K>& 
     A.gd[k][0] = A.gd[k][1] = A.gd[k][2] = z;
   }
   A.l2 = A.l3 = 0.f;
+  A.u = z;
 }
 
 // Rician NLL terms of one measurement (Eq. 9) for the packed path: adds (y - |y_hat|)^2 to l1,
@@ -458,9 +460,13 @@ __device__ __forceinline__ float nll_lane(float yh, float yv, float inv_s2, floa
 // One packed step over measurements (2p, 2p+1). With MASK, lanes whose msk is 0 add nothing.
 // MSE: the data-term accumulators take r = y - y_hat. Rician NLL: they take -dL/dy_hat
 // (unscaled), the same sign convention, and l1..l3 collect the objective's sums.
-template <int K, bool MASK, int LOSS = kLossMSE>
+// With CAL the prediction is y_hat = e^alpha_n B S + beta_n (Eq. 6, B2 = B dup): the adjoint
+// accumulators take q = r e^alpha_n B, A.u collects q S, and uo / ro return q S and r of the
+// two measurements for the per-measurement alpha / beta partials.
+template <int K, bool MASK, int LOSS = kLossMSE, bool CAL = false>
 __device__ __forceinline__ void step2(const VoxP<K>& D, const MeasPair& R, float2 y, float2 msk, AccP<K>& A,
-                                      float inv_s2 = 0.f) {
+                                      float inv_s2 = 0.f, float2 B2 = float2{1.f, 1.f}, float2* uo = nullptr,
+                                      float2* ro = nullptr) {
   const float4 q0 = R.q[0], q1 = R.q[1], q2 = R.q[2], q3 = R.q[3], q4 = R.q[4], q5 = R.q[5];
   const float2 gx = lo2(q0), gy = hi2(q0), gz = lo2(q1), nkpar = hi2(q1);
   const float2 nkperp = lo2(q2), nkd = hi2(q2), ecsf = lo2(q3), egm = hi2(q3);
@@ -477,26 +483,47 @@ __device__ __forceinline__ void step2(const VoxP<K>& D, const MeasPair& R, float
     p[k] = ex2_2(__ffma2_rn(nkd, c2, nkperp));
     T = __ffma2_rn(D.ffin[k], e1[k], __ffma2_rn(D.fomf[k], p[k], T));
   }
-  float2 r;
-  if constexpr (LOSS == kLossMSE) {
-    r = __ffma2_rn(D.nS0, T, y);   // y - y_hat
-    if (MASK) r = __fmul2_rn(r, msk);
-    A.l1 = __ffma2_rn(r, r, A.l1);
+  float2 r, q;
+  if constexpr (CAL) {
+    const float4 q6 = R.q[6];
+    const float2 AB = __fmul2_rn(hi2(q5), B2);                        // e^alpha_n B
+    const float2 S = __fmul2_rn(make_float2(-D.nS0.x, -D.nS0.y), T);
+    const float2 yh = __ffma2_rn(AB, S, lo2(q6));                      // + beta_n
+    if constexpr (LOSS == kLossMSE) {
+      r = __ffma2_rn(make_float2(-1.f, -1.f), yh, y);                  // y - y_hat
+      if (MASK) r = __fmul2_rn(r, msk);
+      A.l1 = __ffma2_rn(r, r, A.l1);
+    } else {
+      r.x = -nll_lane(yh.x, y.x, inv_s2, MASK ? msk.x : 1.f, A.l1.x, A.l2, A.l3);
+      r.y = -nll_lane(yh.y, y.y, inv_s2, MASK ? msk.y : 1.f, A.l1.y, A.l2, A.l3);
+    }
+    q = __fmul2_rn(r, AB);
+    const float2 u = __fmul2_rn(q, S);
+    A.u = __fadd2_rn(A.u, u);
+    *uo = u;
+    *ro = r;
   } else {
-    const float2 yh = __fmul2_rn(D.nS0, T);   // -y_hat
-    r.x = -nll_lane(-yh.x, y.x, inv_s2, MASK ? msk.x : 1.f, A.l1.x, A.l2, A.l3);
-    r.y = -nll_lane(-yh.y, y.y, inv_s2, MASK ? msk.y : 1.f, A.l1.y, A.l2, A.l3);
+    if constexpr (LOSS == kLossMSE) {
+      r = __ffma2_rn(D.nS0, T, y);   // y - y_hat
+      if (MASK) r = __fmul2_rn(r, msk);
+      A.l1 = __ffma2_rn(r, r, A.l1);
+    } else {
+      const float2 yh = __fmul2_rn(D.nS0, T);   // -y_hat
+      r.x = -nll_lane(-yh.x, y.x, inv_s2, MASK ? msk.x : 1.f, A.l1.x, A.l2, A.l3);
+      r.y = -nll_lane(-yh.y, y.y, inv_s2, MASK ? msk.y : 1.f, A.l1.y, A.l2, A.l3);
+    }
+    q = r;
   }
-  A.gcsf = __ffma2_rn(r, ecsf, A.gcsf);
-  A.ggm = __ffma2_rn(r, egm, A.ggm);
-  A.gres = __ffma2_rn(r, eres, A.gres);
+  A.gcsf = __ffma2_rn(q, ecsf, A.gcsf);
+  A.ggm = __ffma2_rn(q, egm, A.ggm);
+  A.gres = __ffma2_rn(q, eres, A.gres);
   const float2 anf = __fmul2_rn(An, D.fin), bno = __fmul2_rn(Bn, D.omf);
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    A.gwa[k] = __ffma2_rn(r, e1[k], A.gwa[k]);
-    A.gwb[k] = __ffma2_rn(r, p[k], A.gwb[k]);
+    A.gwa[k] = __ffma2_rn(q, e1[k], A.gwa[k]);
+    A.gwb[k] = __ffma2_rn(q, p[k], A.gwb[k]);
     const float2 inner = __ffma2_rn(bno, p[k], __fmul2_rn(anf, e1[k]));
-    const float2 w = __fmul2_rn(__fmul2_rn(r, c[k]), inner);
+    const float2 w = __fmul2_rn(__fmul2_rn(q, c[k]), inner);
     A.gd[k][0] = __ffma2_rn(w, gx, A.gd[k][0]);
     A.gd[k][1] = __ffma2_rn(w, gy, A.gd[k][1]);
     A.gd[k][2] = __ffma2_rn(w, gz, A.gd[k][2]);
@@ -534,7 +561,7 @@ __device__ __forceinline__ void step2_b0(const VoxP<K>& D, const float2* __restr
 
 // Fold packed accumulators into the scalar ones (dJ/dS0 from the compartment sums:
 // sum_n q T = f_csf sum q E_csf + ... + sum_k (f_k f_in sum q e1 + f_k (1-f_in) sum q p)).
-template <int K, int LOSS>
+template <int K, int LOSS, bool CAL>
 __device__ __forceinline__ void accp_fold(const Vox<K>& P, const AccP<K>& B, Acc<K>& A) {
   A.gcsf = -(B.gcsf.x + B.gcsf.y);
   A.ggm = -(B.ggm.x + B.ggm.y);
@@ -544,6 +571,7 @@ __device__ __forceinline__ void accp_fold(const Vox<K>& P, const AccP<K>& B, Acc
     A.l2 = B.l2;
     A.l3 = B.l3;
   }
+  if constexpr (CAL) A.u = -(B.u.x + B.u.y);
   float g = P.f[0] * A.gcsf + P.f[1] * A.ggm + P.f[K + 2] * A.gres;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -700,8 +728,10 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_iter_fused(const IterArgs 
   constexpr int NF = K + 3, Q = 4 * K + 5, XF = 4 * K + 3;
   constexpr int NW = kFusedThreads / 32;
   constexpr int VW = 32 / TPV;              // voxels per warp
-  constexpr bool PACKED = (TPV == 1) && !CAL;
-  constexpr bool HOIST = PACKED && K <= 3 && LOSS == kLossMSE;
+  // packed two-measurement steps with one thread per voxel; the calibrated NLL keeps the
+  // scalar loop (its packed form spills and measured slower)
+  constexpr bool PACKED = (TPV == 1) && !(CAL && LOSS == kLossNLL);
+  constexpr bool HOIST = PACKED && K <= 3 && LOSS == kLossMSE && !CAL;
   static_assert(kChunk % TPV == 0, "chunk must split evenly across the voxel's lanes");
   extern __shared__ __align__(16) unsigned char smem[];
   const int Vp = a.Vpad;
@@ -770,8 +800,9 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_iter_fused(const IterArgs 
         fence_proxy_async_smem();
         if (PACKED) {
           const uint32_t tb = static_cast<uint32_t>(NP / 2 * sizeof(MeasPair));
-          mbar_expect_tx(&s_bar, tb);
+          mbar_expect_tx(&s_bar, tb + (CAL ? kNGrid * 4u : 0u));
           tma_bulk_g2s(s_tab, a.table2 + gr.table2_off, tb, &s_bar);
+          if (CAL) tma_bulk_g2s(s_blr, a.gparams + gr.gp_off + 4 + 2 * gr.N4, kNGrid * 4u, &s_bar);
         } else {
           const uint32_t tb = static_cast<uint32_t>(N * sizeof(MeasRow));
           mbar_expect_tx(&s_bar, tb + (CAL ? kNGrid * 4u : 0u));
@@ -857,7 +888,34 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_iter_fused(const IterArgs 
         // leading pairs of b = 0 measurements (the group's table starts with them); the NLL
         // still needs the Bessel terms there, so it takes them as ordinary pairs
         const int i0 = (LOSS == kLossMSE) ? max(0, min(kChunk / 2, gr.nb0p - j * (kChunk / 2))) : 0;
-        if (act && cnt == kChunk && i0 == 0) {
+        if constexpr (CAL) {
+          // two packed steps (four measurements) per reduce-scatter of the alpha / beta
+          // partials; the accumulators hold the negated values, so the stores negate
+          const float2 B2 = make_float2(B, B);
+#pragma unroll 1
+          for (int i = 0; i < kChunk / 2; i += 2) {
+            float uu[4], rv[4];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int pi = i + h;
+              float2 u = make_float2(0.f, 0.f), r = make_float2(0.f, 0.f);
+              if (act && 2 * pi < cnt)
+                step2<K, true, LOSS, true>(DP, tab2[pi], yc2[pi * VW], make_float2(1.f, (2 * pi + 1 < cnt) ? 1.f : 0.f),
+                                           AP, inv_s2, B2, &u, &r);
+              uu[2 * h] = u.x;
+              uu[2 * h + 1] = u.y;
+              rv[2 * h] = r.x;
+              rv[2 * h + 1] = r.y;
+            }
+            const float su = warp_scatter_sum<4>(uu);
+            const float sr = warp_scatter_sum<4>(rv);
+            const int m = lane >> 3;
+            if ((lane & 7) == 0 && 2 * i + m < cnt) {
+              s_ab[(warp * 2) * a.Nmax + j * kChunk + 2 * i + m] = -su;
+              s_ab[(warp * 2 + 1) * a.Nmax + j * kChunk + 2 * i + m] = -sr;
+            }
+          }
+        } else if (act && cnt == kChunk && i0 == 0) {
 #pragma unroll 2
           for (int i = 0; i < kChunk / 2; ++i)
             step2<K, false, LOSS>(DP, tab2[i], yc2[i * VW], make_float2(1.f, 1.f), AP, inv_s2);
@@ -936,7 +994,7 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_iter_fused(const IterArgs 
     load_theta<K>(a.theta, Vp, slot, act, th);
     if constexpr (HOIST) load_moments<Q>(a, slot, writer, mq, vq);
     transform<K>(th, P);
-    if constexpr (PACKED) accp_fold<K, LOSS>(P, AP, A);
+    if constexpr (PACKED) accp_fold<K, LOSS, CAL>(P, AP, A);
     acc_reduce_tpv<K, TPV>(A);
 
     // ---- data-term gradient and value

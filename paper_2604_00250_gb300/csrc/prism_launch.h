@@ -40,6 +40,7 @@ struct GroupArgs {
   float* gv;
   float* gparams;
   MeasRow* table;
+  MeasPair* table2;   // the paired copy (its e^alpha_n and beta_n follow the rows)
   const int32_t* slot_of_grid;
   double* hist;               // [H][G] loss history
   int32_t hist_len;
