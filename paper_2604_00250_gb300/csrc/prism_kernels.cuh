@@ -723,14 +723,23 @@ __device__ __forceinline__ void finalize_groups(const IterArgs& a, double (*s_su
   }
 }
 
+// CTAs per SM the fused kernel is compiled for: 4 (128 registers per thread) where the voxel
+// state fits, 3 (170 registers) for five fibers and for the packed NLL / calibrated variants,
+// which spill at 128 and measured 7-54 % faster at 3.
 template <int K, int TPV, int LOSS, bool CAL>
-__global__ void __launch_bounds__(kFusedThreads, 4) k_iter_fused(const IterArgs a) {
+constexpr int fused_min_blocks() {
+  return ((K >= 5) || (TPV == 1 && (LOSS == kLossNLL || CAL))) ? 3 : 4;
+}
+
+template <int K, int TPV, int LOSS, bool CAL>
+__global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<K, TPV, LOSS, CAL>())) k_iter_fused(const IterArgs a) {
   constexpr int NF = K + 3, Q = 4 * K + 5, XF = 4 * K + 3;
   constexpr int NW = kFusedThreads / 32;
   constexpr int VW = 32 / TPV;              // voxels per warp
-  // packed two-measurement steps with one thread per voxel; the calibrated NLL keeps the
-  // scalar loop (its packed form spills and measured slower)
-  constexpr bool PACKED = (TPV == 1) && !(CAL && LOSS == kLossNLL);
+  // packed two-measurement steps with one thread per voxel; the calibrated NLL with five
+  // fibers keeps the scalar loop (its packed form spills even at 170 registers and measured
+  // 11 % slower)
+  constexpr bool PACKED = (TPV == 1) && !(CAL && LOSS == kLossNLL && K >= 5);
   constexpr bool HOIST = PACKED && K <= 3 && LOSS == kLossMSE && !CAL;
   static_assert(kChunk % TPV == 0, "chunk must split evenly across the voxel's lanes");
   extern __shared__ __align__(16) unsigned char smem[];
