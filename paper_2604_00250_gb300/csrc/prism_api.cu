@@ -105,6 +105,10 @@ struct prism_handle {
   MeasPair* d_table2 = nullptr;
   int64_t tab2_pairs = 0;
   double *d_tile_red = nullptr, *d_part2 = nullptr, *d_gred = nullptr, *d_gloss = nullptr;
+  double* d_bscratch = nullptr;      // bias-gradient partial contractions (calibration only)
+  int64_t* d_bs_off = nullptr;       // [G][2] offsets into d_bscratch
+  int max_nx = 0, max_ny = 0;
+  int32_t* d_gdone = nullptr;
   double *d_gprior = nullptr, *d_hist = nullptr;
   IterArgs ia{};
   GroupArgs ga{};
@@ -317,6 +321,11 @@ void fill_args(prism_handle* h) {
   g.gparams = h->d_gparams;
   g.table = h->d_table;
   g.table2 = h->d_table2;
+  g.bscratch = h->d_bscratch;
+  g.gdone = h->d_gdone;
+  g.bs_off = h->d_bs_off;
+  g.max_nx = h->max_nx;
+  g.max_ny = h->max_ny;
   g.slot_of_grid = h->d_slot_of_grid;
   g.hist = h->d_hist;
   g.hist_len = kHistLen;
@@ -646,6 +655,25 @@ int init_impl(prism_handle* h, const prism_volume* vols, int n_vols, cudaStream_
   RC(h->alloc(&h->d_split_off, G));
   RC(h->alloc(&h->d_part2, static_cast<size_t>(tot_split) * h->max_e));
   RC(h->alloc(&h->d_counters, static_cast<size_t>(G) * nce));
+  RC(h->alloc(&h->d_gdone, 1));
+  CK(cudaMemsetAsync(h->d_gdone, 0, sizeof(int32_t), st));
+  if (h->cal) {
+    // per group [nx][ny][8] then [nx][8][8] doubles for the separable bias-field adjoint
+    std::vector<int64_t> bs(2 * static_cast<size_t>(G));
+    int64_t tot = 0;
+    for (int g = 0; g < G; ++g) {
+      const GroupDev& gr = h->groups[g];
+      bs[2 * g] = tot;
+      tot += static_cast<int64_t>(gr.nx) * gr.ny * kGrid;
+      bs[2 * g + 1] = tot;
+      tot += static_cast<int64_t>(gr.nx) * kGrid * kGrid;
+      h->max_nx = std::max(h->max_nx, gr.nx);
+      h->max_ny = std::max(h->max_ny, gr.ny);
+    }
+    RC(h->alloc(&h->d_bscratch, tot));
+    RC(h->alloc(&h->d_bs_off, 2 * static_cast<size_t>(G)));
+    RC(upload(h->d_bs_off, bs, st));
+  }
   if (!o.fused) {
     RC(h->alloc(&h->d_yhat, h->ypack_len));
     RC(h->alloc(&h->d_r, h->ypack_len));

@@ -273,47 +273,102 @@ __global__ void __launch_bounds__(256) k_group_reduce(const IterArgs a, const Gr
   if (threadIdx.x == 0) g.counters[gi * nce + ce] = 0;
 }
 
-// dJ/db_lr[c] = sum_x w_c(x) dJ/dU(x) over the voxels whose trilinear stencil holds corner c.
-__global__ void __launch_bounds__(256) k_bias_grad(const IterArgs a, const GroupArgs g) {
-  __shared__ double s[256];
-  const int gi = blockIdx.y, c = blockIdx.x;
+// dJ/db_lr[c] = sum_x w_c(x) dJ/dU(x): the adjoint of the trilinear upsampling. Its weights
+// factor per axis, w_c(x, y, z) = w_cx(x) w_cy(y) w_cz(z), so the sum is three contractions
+// in a fixed order: over z (per (x, y) line), then y, then x; each grid voxel is read once.
+// Axis weights as in tri_weights: u = clamp((i + .5) 8 / n - .5, 0, 7), i0 = min(floor u, 6),
+// corner i0 takes 1 - (u - i0) and corner i0 + 1 takes u - i0.
+__device__ __forceinline__ void axis_weight(int i, int n, int& i0, float& w) {
+  float u = (i + 0.5f) * (8.f / n) - 0.5f;
+  u = fminf(fmaxf(u, 0.f), 7.f);
+  i0 = min(static_cast<int>(floorf(u)), 6);
+  w = u - i0;
+}
+
+// The voxels whose weight for corner c of an n-voxel axis can be nonzero (with a margin of
+// one): [lo, hi].
+__device__ __forceinline__ void axis_support(int c, int n, int& lo, int& hi) {
+  const float sc = n / 8.f;
+  lo = (c == 0) ? 0 : max(0, static_cast<int>(floorf((c - 0.5f) * sc - 0.5f)) - 1);
+  hi = (c == kGrid - 1) ? n - 1 : min(n - 1, static_cast<int>(ceilf((c + 1.5f) * sc - 0.5f)) + 1);
+}
+__device__ __forceinline__ float axis_corner_weight(int i, int n, int c) {
+  int i0;
+  float w;
+  axis_weight(i, n, i0, w);
+  return (c == i0) ? 1.f - w : ((c == i0 + 1) ? w : 0.f);
+}
+
+// Pass 1: G1[x][y][cz] = sum_z w_cz(z) dJ/dU(x, y, z); one warp per (x, y) line, its lanes
+// strided over z, then a fixed-order butterfly over the lanes (FP32: at most 1023 terms).
+__global__ void __launch_bounds__(128) k_bias_grad_z(const IterArgs a, const GroupArgs g) {
+  const int gi = blockIdx.y;
+  const GroupDev gr = a.groups[gi];
+  const int line = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (!gr.calib || line >= gr.nx * gr.ny) return;   // warp-uniform
+  double* G1 = g.bscratch + g.bs_off[2 * gi];
+  float acc[kGrid];
+#pragma unroll
+  for (int c = 0; c < kGrid; ++c) acc[c] = 0.f;
+  const int32_t* sog = g.slot_of_grid + gr.grid_off + static_cast<int64_t>(line) * gr.nz;
+  for (int z = lane; z < gr.nz; z += 32) {
+    const int slot = sog[z];
+    if (slot < 0) continue;
+    int k0;
+    float wz;
+    axis_weight(z, gr.nz, k0, wz);
+    const float u = a.gU[slot];
+#pragma unroll
+    for (int c = 0; c < kGrid - 1; ++c)
+      if (c == k0) {
+        acc[c] = fmaf(1.f - wz, u, acc[c]);
+        acc[c + 1] = fmaf(wz, u, acc[c + 1]);
+      }
+  }
+#pragma unroll
+  for (int c = 0; c < kGrid; ++c) {
+    const float v = warp_sum_range<1, 16>(acc[c]);
+    if (lane == 0) G1[static_cast<int64_t>(line) * kGrid + c] = v;
+  }
+}
+
+// Pass 2: G2[x][cy][cz] = sum_y w_cy(y) G1[x][y][cz]; one thread per (x, cy, cz), over the
+// support of cy only.
+__global__ void __launch_bounds__(128) k_bias_grad_y(const IterArgs a, const GroupArgs g) {
+  const int gi = blockIdx.y;
   const GroupDev gr = a.groups[gi];
   if (!gr.calib) return;
-  const int cc[3] = {c / 64, (c / 8) % 8, c % 8};
-  const int n[3] = {gr.nx, gr.ny, gr.nz};
-  int lo[3], hi[3];
-#pragma unroll
-  for (int ax = 0; ax < 3; ++ax) {
-    const float sc = n[ax] / 8.f;
-    lo[ax] = (cc[ax] == 0) ? 0 : max(0, static_cast<int>(floorf((cc[ax] - 0.5f) * sc - 0.5f)) - 1);
-    hi[ax] = (cc[ax] == 7) ? n[ax] - 1 : min(n[ax] - 1, static_cast<int>(ceilf((cc[ax] + 1.5f) * sc - 0.5f)) + 1);
-  }
-  const int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1, ez = hi[2] - lo[2] + 1;
-  const int tot = ex * ey * ez;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= gr.nx * kGrid * kGrid) return;
+  const int x = e / (kGrid * kGrid), cy = (e / kGrid) % kGrid, cz = e % kGrid;
+  const double* G1 = g.bscratch + g.bs_off[2 * gi];
+  double* G2 = g.bscratch + g.bs_off[2 * gi + 1];
+  int lo, hi;
+  axis_support(cy, gr.ny, lo, hi);
   double acc = 0.0;
-  for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-    const int x = lo[0] + i / (ey * ez);
-    const int y = lo[1] + (i / ez) % ey;
-    const int z = lo[2] + i % ez;
-    const int slot = g.slot_of_grid[gr.grid_off + (static_cast<int64_t>(x) * gr.ny + y) * gr.nz + z];
-    if (slot < 0) continue;
-    const TriW tw = tri_weights(x, y, z, gr.nx, gr.ny, gr.nz);
-    const int b[3] = {tw.base / 64, (tw.base / 8) % 8, tw.base % 8};
-    float w = 1.f;
-#pragma unroll
-    for (int ax = 0; ax < 3; ++ax) {
-      const int d = cc[ax] - b[ax];
-      w *= (d == 0) ? 1.f - tw.w[ax] : ((d == 1) ? tw.w[ax] : 0.f);
-    }
-    if (w != 0.f) acc += static_cast<double>(w) * a.gU[slot];
+  for (int y = lo; y <= hi; ++y) {
+    const float w = axis_corner_weight(y, gr.ny, cy);
+    if (w != 0.f) acc += static_cast<double>(w) * G1[(static_cast<int64_t>(x) * gr.ny + y) * kGrid + cz];
   }
-  s[threadIdx.x] = acc;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
-    __syncthreads();
+  G2[(static_cast<int64_t>(x) * kGrid + cy) * kGrid + cz] = acc;
+}
+
+// Pass 3: dJ/db_lr[cx][cy][cz] = sum_x w_cx(x) G2[x][cy][cz]; one thread per corner.
+__global__ void __launch_bounds__(kNGrid) k_bias_grad_x(const IterArgs a, const GroupArgs g) {
+  const int gi = blockIdx.x;
+  const GroupDev gr = a.groups[gi];
+  if (!gr.calib) return;
+  const int c = threadIdx.x;
+  const int cx = c / (kGrid * kGrid), cyz = c % (kGrid * kGrid);
+  const double* G2 = g.bscratch + g.bs_off[2 * gi + 1];
+  int lo, hi;
+  axis_support(cx, gr.nx, lo, hi);
+  double acc = 0.0;
+  for (int x = lo; x <= hi; ++x) {
+    const float w = axis_corner_weight(x, gr.nx, cx);
+    if (w != 0.f) acc += static_cast<double>(w) * G2[static_cast<int64_t>(x) * kGrid * kGrid + cyz];
   }
-  if (threadIdx.x == 0) g.gred[gr.gp_off + 4 + 2 * gr.N4 + c] = s[0];
+  g.gred[gr.gp_off + 4 + 2 * gr.N4 + c] = acc;
 }
 
 // Group finalisation (one block): objective with calibration regularisers (reading R11),
@@ -321,12 +376,13 @@ __global__ void __launch_bounds__(256) k_bias_grad(const IterArgs a, const Group
 // mode bit 0: loss; bit 1: Adam + step; bit 2: export gradients.
 __global__ void __launch_bounds__(256) k_group_adam(const IterArgs a, const GroupArgs g, int mode) {
   __shared__ double s[256];
-  __shared__ int s_bad;
+  __shared__ int s_bad, s_last;
   const int tid = threadIdx.x;
   if (tid == 0) s_bad = 0;
   const int step = *a.step;
   const float stepsz = a.adamc[0], isbc2 = a.adamc[1];
-  for (int gi = 0; gi < g.G; ++gi) {
+  // one block per group; the last block to finish advances the step counter
+  for (int gi = blockIdx.x; gi < g.G; gi += gridDim.x) {
     const GroupDev gr = a.groups[gi];
     const int base = gr.gp_off;
     const int N = gr.N, N4 = gr.N4;
@@ -408,8 +464,18 @@ __global__ void __launch_bounds__(256) k_group_adam(const IterArgs a, const Grou
     }
     __syncthreads();
   }
-  if ((mode & 2) && tid == 0) {
-    if (s_bad) atomicOr(a.status, kStNonfinite);
+  if (tid == 0 && s_bad) atomicOr(a.status, kStNonfinite);
+  if (!(mode & 2)) return;
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    s_last = (atomicAdd(g.gdone, 1) == static_cast<int>(gridDim.x) - 1);
+  }
+  __syncthreads();
+  if (!s_last || tid != 0) return;
+  __threadfence();
+  *g.gdone = 0;
+  {
     *const_cast<int32_t*>(a.step) = step + 1;
     // constants of the next iteration, t = step + 2 (bias corrections in double)
     const double t2 = static_cast<double>(step) + 2.0;
@@ -452,11 +518,13 @@ cudaError_t launch_group_reduce(const IterArgs& a, const GroupArgs& g, int what,
   return cudaGetLastError();
 }
 cudaError_t launch_bias_grad(const IterArgs& a, const GroupArgs& g, cudaStream_t st) {
-  k_bias_grad<<<dim3(kNGrid, g.G), 256, 0, st>>>(a, g);
+  k_bias_grad_z<<<dim3(nblk(static_cast<int64_t>(g.max_nx) * g.max_ny, 4), g.G), 128, 0, st>>>(a, g);
+  k_bias_grad_y<<<dim3(nblk(static_cast<int64_t>(g.max_nx) * kGrid * kGrid, 128), g.G), 128, 0, st>>>(a, g);
+  k_bias_grad_x<<<g.G, kNGrid, 0, st>>>(a, g);
   return cudaGetLastError();
 }
 cudaError_t launch_group_adam(const IterArgs& a, const GroupArgs& g, int mode, cudaStream_t st) {
-  k_group_adam<<<1, 256, 0, st>>>(a, g, mode);
+  k_group_adam<<<g.G, 256, 0, st>>>(a, g, mode);
   return cudaGetLastError();
 }
 cudaError_t launch_loss(const IterArgs& a, const PlainArgs& p, int loss, cudaStream_t st) {

@@ -47,6 +47,10 @@ struct GroupArgs {
   float* gexport;             // packed group gradients for the caller (or null)
   int32_t loss_mode;          // kLossMSE / kLossNLL
   float w_alpha, w_beta, w_blr;
+  double* bscratch;           // bias-gradient partial contractions (see k_bias_grad_*)
+  const int64_t* bs_off;      // [G][2] offsets of a group's [nx][ny][8] and [nx][8][8] parts
+  int32_t max_nx, max_ny;     // largest grid extents over the groups
+  int32_t* gdone;             // blocks of k_group_adam that finished (last one resets it)
 };
 
 cudaError_t launch_group_reduce(const IterArgs& a, const GroupArgs& g, int what, cudaStream_t st);
