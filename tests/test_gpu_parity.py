@@ -297,3 +297,23 @@ def test_interleaved_b0_scheme(loss, tpv):
     ref = np.concatenate([t.numpy() for t in res.theta])
     assert float(np.max(np.abs(f.params_host() - ref))) < 3e-4
     f.close()
+
+
+@pytest.mark.parametrize("loss,cal", [("mse", False), ("nll", False), ("mse", True), ("nll", True)])
+def test_adam_steps_five_fibers(loss, cal):
+    """K = 5 (the paper's DiSCo1 setting) through the fused kernel with one thread per voxel:
+    packed steps for the MSE, NLL and calibrated MSE, the scalar loop for the calibrated NLL,
+    all compiled for 3 CTAs per SM."""
+    vols = _problem(cal)
+    K = 5
+    inits = inits_for(vols, K, 9)
+    kw = dict(K=K, loss=loss, calibration=cal, patch_dim=4, lam_sp=0.01, lam_dir=0.005, fused=1, use_graph=1,
+              threads_per_voxel=1, lam_order=0.01)
+    f, ovs = make_pair(vols, inits, **kw)
+    f.step(3)
+    f.sync()
+    res = O.fit(ovs, [torch.as_tensor(t).double() for t in inits], 3)
+    np.testing.assert_allclose(f.loss_history(), res.loss_history, rtol=1e-5)
+    ref = np.concatenate([t.numpy() for t in res.theta])
+    assert float(np.max(np.abs(f.params_host() - ref))) < 3e-4
+    f.close()
