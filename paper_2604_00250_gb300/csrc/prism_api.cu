@@ -411,8 +411,7 @@ static int32_t meas_order(const prism_volume& v, bool cal, std::vector<int32_t>&
 }
 
 struct Plan {
-  std::vector<int32_t> slot_of_vox, vox_of_slot, nbr, slot_of_grid;
-  std::vector<uint32_t> vcoord, vflag;
+  std::vector<int32_t> slot_of_vox, slot_of_grid;
   std::vector<int64_t> row_off;
 };
 
@@ -525,57 +524,8 @@ int build_plan(prism_handle* h, const prism_volume* vols, int n_vols, Plan& pl) 
   h->tab_rows = tab;
   h->yhat_off[n_vols] = yh;
   h->yhat_len = yh;
-  // per-slot data
-  const int Vp = h->Vpad;
-  pl.vox_of_slot.assign(Vp, -1);
-  pl.vcoord.assign(Vp, 0);
-  pl.vflag.assign(Vp, 0);
-  const int nnb = h->opt.connectivity;
-  pl.nbr.assign(static_cast<size_t>(nnb) * Vp, -1);
-  // the six face neighbours first (their bits 0-5 also flag the bias TV pairs), then the
-  // edge and corner neighbours of the 3x3x3 cube for 26-connectivity
-  int off[26][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
-  {
-    int e = 6;
-    for (int i = -1; i <= 1; ++i)
-      for (int j = -1; j <= 1; ++j)
-        for (int k = -1; k <= 1; ++k)
-          if (std::abs(i) + std::abs(j) + std::abs(k) > 1) {
-            off[e][0] = i;
-            off[e][1] = j;
-            off[e][2] = k;
-            ++e;
-          }
-  }
-  for (int g = 0; g < n_vols; ++g) {
-    const prism_volume& v = vols[g];
-    const GroupDev& gr = h->groups[g];
-    for (int x = 0; x < v.nx; ++x)
-      for (int y = 0; y < v.ny; ++y)
-        for (int z = 0; z < v.nz; ++z) {
-          const int64_t gi = (static_cast<int64_t>(x) * v.ny + y) * v.nz + z;
-          if (vidx[g][gi] < 0) continue;
-          const int slot = pl.slot_of_grid[gr.grid_off + gi];
-          pl.vox_of_slot[slot] = static_cast<int32_t>(h->vox0[g] + vidx[g][gi]);
-          pl.vcoord[slot] = static_cast<uint32_t>(x) | (static_cast<uint32_t>(y) << 10) | (static_cast<uint32_t>(z) << 20);
-          const int patch = h->tiles[slot / TV].patch;
-          uint32_t fl = 0;
-          int cnt = 0;
-          for (int e = 0; e < nnb; ++e) {
-            const int xx = x + off[e][0], yy = y + off[e][1], zz = z + off[e][2];
-            if (xx < 0 || yy < 0 || zz < 0 || xx >= v.nx || yy >= v.ny || zz >= v.nz) continue;
-            const int64_t gj = (static_cast<int64_t>(xx) * v.ny + yy) * v.nz + zz;
-            if (vidx[g][gj] < 0) continue;
-            if (e < 6) fl |= 1u << e;   // TV neighbour inside the mask (any patch)
-            const int sj = pl.slot_of_grid[gr.grid_off + gj];
-            if (h->tiles[sj / TV].patch == patch) {
-              pl.nbr[static_cast<size_t>(e) * Vp + slot] = sj;
-              ++cnt;
-            }
-          }
-          pl.vflag[slot] = fl | (static_cast<uint32_t>(cnt) << 8);
-        }
-  }
+  // the per-slot tables (mask-order index, coordinates, neighbour slots and flags) are built
+  // on the device from slot_of_grid (launch_slot_data)
   return PRISM_OK;
 }
 
@@ -705,12 +655,10 @@ int init_impl(prism_handle* h, const prism_volume* vols, int n_vols, cudaStream_
   // metadata
   RC(upload(h->d_tiles, h->tiles, st));
   RC(upload(h->d_groups, h->groups, st));
-  RC(upload(h->d_nbr, pl.nbr, st));
-  RC(upload(h->d_vcoord, pl.vcoord, st));
-  RC(upload(h->d_vflag, pl.vflag, st));
   RC(upload(h->d_slot_of_vox, pl.slot_of_vox, st));
-  RC(upload(h->d_vox_of_slot, pl.vox_of_slot, st));
   RC(upload(h->d_slot_of_grid, pl.slot_of_grid, st));
+  CK(launch_slot_data(h->d_tiles, h->d_groups, h->G, h->groups.data(), h->d_slot_of_grid, h->d_slot_of_vox, h->V,
+                      Vp, h->TV, h->opt.connectivity, h->d_vox_of_slot, h->d_vcoord, h->d_vflag, h->d_nbr, st));
   RC(upload(h->d_row_off, pl.row_off, st));
   RC(upload(h->d_order, h->order, st));
   RC(upload(h->d_split_off, split_off, st));

@@ -120,6 +120,59 @@ __global__ void k_pair_table(const MeasRow* rows, int N, int NP, MeasPair* out) 
   out[pidx] = mp;
 }
 
+// Per-slot tables of one volume from its grid -> slot map (one thread per grid position):
+// packed coordinates, flags (bits 0-5: the face neighbour in +x, -x, +y, -y, +z, -z is in the
+// mask, any patch; bits 8-12: the count of neighbours in the same patch) and the neighbour
+// slots in the same patch: the six faces first, then the edges and corners of the 3x3x3 cube
+// in (i, j, k) loop order.
+__global__ void k_slot_data(const Tile* __restrict__ tiles, const GroupDev* __restrict__ groups, int g,
+                            const int32_t* __restrict__ slot_of_grid, int Vp, int TV, int nnb,
+                            uint32_t* __restrict__ vcoord, uint32_t* __restrict__ vflag, int32_t* __restrict__ nbr) {
+  const GroupDev gr = groups[g];
+  const int64_t ng = static_cast<int64_t>(gr.nx) * gr.ny * gr.nz;
+  const int64_t gi = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (gi >= ng) return;
+  const int32_t* sog = slot_of_grid + gr.grid_off;
+  const int slot = sog[gi];
+  if (slot < 0) return;
+  const int z = static_cast<int>(gi % gr.nz), y = static_cast<int>((gi / gr.nz) % gr.ny),
+            x = static_cast<int>(gi / (static_cast<int64_t>(gr.nz) * gr.ny));
+  vcoord[slot] = static_cast<uint32_t>(x) | (static_cast<uint32_t>(y) << 10) | (static_cast<uint32_t>(z) << 20);
+  const int patch = tiles[slot / TV].patch;
+  uint32_t fl = 0;
+  int cnt = 0;
+  int next = 6;   // index of the next edge / corner neighbour
+  for (int pass = 0; pass < 2; ++pass)
+    for (int i = -1; i <= 1; ++i)
+      for (int j = -1; j <= 1; ++j)
+        for (int k = -1; k <= 1; ++k) {
+          const int l1 = abs(i) + abs(j) + abs(k);
+          if (l1 == 0 || (pass == 0) != (l1 == 1)) continue;
+          int e;
+          if (pass == 0) {
+            e = (i != 0) ? (i > 0 ? 0 : 1) : (j != 0) ? (j > 0 ? 2 : 3) : (k > 0 ? 4 : 5);   // +x -x +y -y +z -z
+          } else {
+            if (next >= nnb) continue;
+            e = next++;
+          }
+          const int xx = x + i, yy = y + j, zz = z + k;
+          if (xx < 0 || yy < 0 || zz < 0 || xx >= gr.nx || yy >= gr.ny || zz >= gr.nz) continue;
+          const int sj = sog[(static_cast<int64_t>(xx) * gr.ny + yy) * gr.nz + zz];
+          if (sj < 0) continue;
+          if (e < 6) fl |= 1u << e;
+          if (tiles[sj / TV].patch == patch) {
+            nbr[static_cast<size_t>(e) * Vp + slot] = sj;
+            ++cnt;
+          }
+        }
+  vflag[slot] = fl | (static_cast<uint32_t>(cnt) << 8);
+}
+
+__global__ void k_vox_of_slot(const int32_t* __restrict__ slot_of_vox, int64_t V, int32_t* __restrict__ vox_of_slot) {
+  const int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (v < V) vox_of_slot[slot_of_vox[v]] = static_cast<int32_t>(v);
+}
+
 // Row gather: dst[i][:] = src[rows[i]][:] (slab volumes cut from a whole volume).
 __global__ void k_gather_rows(const float* __restrict__ src, const int64_t* __restrict__ rows, int64_t n, int len,
                               float* __restrict__ dst) {
@@ -556,6 +609,21 @@ cudaError_t launch_pack(const IterArgs& a, const float* sig, const float* b0mean
   (void)bad;
   if (tile_end <= tile_begin) return cudaSuccess;
   k_pack<<<tile_end - tile_begin, 256, 0, st>>>(a, sig, b0mean, vox_of_slot, order, vox0, tile_begin, N, ypack);
+  return cudaGetLastError();
+}
+cudaError_t launch_slot_data(const Tile* tiles, const GroupDev* groups, int G, const GroupDev* host_groups,
+                             const int32_t* slot_of_grid, const int32_t* slot_of_vox, int64_t V, int Vp, int TV, int nnb,
+                             int32_t* vox_of_slot, uint32_t* vcoord, uint32_t* vflag, int32_t* nbr, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(vox_of_slot, 0xff, sizeof(int32_t) * Vp, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(vcoord, 0, sizeof(uint32_t) * Vp, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(vflag, 0, sizeof(uint32_t) * Vp, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(nbr, 0xff, sizeof(int32_t) * static_cast<size_t>(nnb) * Vp, st);
+  if (e != cudaSuccess) return e;
+  if (V > 0) k_vox_of_slot<<<nblk(V, 256), 256, 0, st>>>(slot_of_vox, V, vox_of_slot);
+  for (int g = 0; g < G; ++g) {
+    const int64_t ng = static_cast<int64_t>(host_groups[g].nx) * host_groups[g].ny * host_groups[g].nz;
+    k_slot_data<<<nblk(ng, 256), 256, 0, st>>>(tiles, groups, g, slot_of_grid, Vp, TV, nnb, vcoord, vflag, nbr);
+  }
   return cudaGetLastError();
 }
 cudaError_t launch_gather_rows(const float* src, const int64_t* rows, int64_t n, int len, float* dst,

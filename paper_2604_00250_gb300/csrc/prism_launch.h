@@ -67,6 +67,9 @@ cudaError_t launch_sigma_init(const double* part, int nblocks, int64_t V, int nb
 cudaError_t launch_pack(const IterArgs& a, const float* sig, const float* b0mean, const int32_t* vox_of_slot,
                         const int32_t* order, int64_t vox0, int tile_begin, int tile_end, int N, float* ypack,
                         int* bad, cudaStream_t st);
+cudaError_t launch_slot_data(const Tile* tiles, const GroupDev* groups, int G, const GroupDev* host_groups,
+                             const int32_t* slot_of_grid, const int32_t* slot_of_vox, int64_t V, int Vp, int TV, int nnb,
+                             int32_t* vox_of_slot, uint32_t* vcoord, uint32_t* vflag, int32_t* nbr, cudaStream_t st);
 cudaError_t launch_gather_rows(const float* src, const int64_t* rows, int64_t n, int len, float* dst,
                                cudaStream_t st);
 cudaError_t launch_table(const float* bvals, const float* bvecs, int N, MeasRow* rows, cudaStream_t st);
