@@ -130,3 +130,26 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(L, "LIB_PATH", str(tmp_path / "absent.so"))
     with pytest.raises(ImportError):
         L.load()
+
+
+@pytest.mark.parametrize("slab,overlap,code", [(0, 0, 1), (10, -1, 1), (10, 6, 1)])
+def test_slab_driver_validation(prism, slab, overlap, code):
+    """prism_fit_init_slabs rejects a slab of no slices, a negative overlap and an overlap
+    above half a slab before any device work."""
+    vol = _vol(np.ones((2, 2, 12), np.uint8))
+    with pytest.raises(prism.PrismError) as e:
+        prism.Fitter(vol, prism.options(), slabs=(slab, overlap))
+    assert e.value.code == code
+
+
+def test_slab_driver_empty_mask(prism):
+    vol = _vol(np.zeros((2, 2, 12), np.uint8))
+    with pytest.raises(prism.PrismError) as e:
+        prism.Fitter(vol, prism.options(), slabs=(6, 2))
+    assert e.value.code == 2
+
+
+def test_readout_entry_points_reject_null_handles(prism):
+    lib = prism._lib.load()
+    assert lib.prism_get_fibers(None, None, None, None, ctypes.c_float(0.15), 0, None) == 1
+    assert lib.prism_stitch_slabs(None, None, None, None, None, 0, None) == 1
