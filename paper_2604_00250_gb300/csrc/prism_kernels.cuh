@@ -390,9 +390,10 @@ __device__ __forceinline__ void fiber_weights(const Vox<K>& P, float (&ffin)[K],
 }
 
 // ---------------------------------------------------------------------------
-// Packed path (one thread per voxel, MSE, no calibration): two measurements per step in
-// f32x2 arithmetic. Voxel constants are held duplicated; accumulators are float2 and are
-// folded after the loop. The residual is taken as y - y_hat (signs restored when folding).
+// Packed path (one thread per voxel; MSE or NLL, with or without calibration): two
+// measurements per step in f32x2 arithmetic. Voxel constants are held duplicated; accumulators
+// are float2 and are folded after the loop. The residual is taken as y - y_hat (signs
+// restored when folding).
 // ---------------------------------------------------------------------------
 template <int K>
 struct VoxP {
