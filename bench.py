@@ -374,6 +374,42 @@ def run_calibrated(args):
     return 0
 
 
+def run_slabs(args):
+    """The paper's whole-brain pipeline (Sec. 3 "Configuration"): the HCP-shaped brain cut into
+    30-slice slabs with a 5-slice overlap, K = 3, MSE with the full prior suite, Rprop (the
+    paper's solver), 100 iterations per slab, then the stitched whole-volume maps. All slabs are one batch. Times the whole job
+    from pinned host buffers (set-up, iterations, stitch, read-out) with the wall clock."""
+    import types
+    import torch
+    import paper_2604_00250_gb300 as prism
+    vol = make_brain(args.seed, "cuda")
+    sig_host = torch.empty(vol.signal.shape, dtype=torch.float32, pin_memory=True)
+    sig_host.copy_(torch.as_tensor(vol.signal))
+    vh = types.SimpleNamespace(mask=vol.mask, signal=sig_host, bvals=vol.bvals, bvecs=vol.bvecs, init=None)
+    opts = prism.options(K=K_FIB, loss="mse", patch_dim=16, lam_orphan=0.01, lam_order=0.01, optimizer="rprop",
+                         **PRIORS)
+    iters = 100
+    times = []
+    for rep in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        f = prism.Fitter(vh, opts, slabs=(30, 5))
+        f.step(iters)
+        s0, fr, fin, d = f.stitch()
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+        n_slab_vox, n_slabs = f.n_vox, f.n_groups
+        f.close()
+    dt = min(times)
+    line = {"workload": "hcp_shaped_brain_slabs_30_overlap_5_K3_mse_full_priors_rprop_100_iterations",
+            "voxels": int(s0.shape[0]), "slabs": n_slabs, "slab_voxels": n_slab_vox, "iterations": iters,
+            "seconds": dt, "value": n_slab_vox * iters / dt, "unit": "slab voxel-iterations/s",
+            "timing": "wall clock, pinned host signal, set-up + iterations + stitch + read-out, best of 2",
+            "paper_context": "the paper reports about 12 minutes for this pipeline on an RTX A6000"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_crossing(args):
     """Quality of the fit on the crossing-fiber benchmark layout (16 angles + single-fiber
     controls, N = 193) at each SNR and both data terms: one JSON line per run with the
@@ -420,9 +456,10 @@ def main():
     ap.add_argument("--no-unfused", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="brain", choices=["brain", "crossing", "bundle", "multi"],
+    ap.add_argument("--workload", default="brain", choices=["brain", "crossing", "bundle", "multi", "slabs"],
                     help="crossing: fit quality on the crossing-fiber benchmark layout; bundle / multi: "
-                         "speed of the calibrated NLL configurations (not the headline)")
+                         "speed of the calibrated NLL configurations; slabs: the whole-brain slab "
+                         "pipeline (not the headline)")
     ap.add_argument("--cross-snr", type=float, nargs="+", default=[10.0, 30.0, 50.0])
     ap.add_argument("--cross-voxels", type=int, default=200, help="voxels per angle (and single-fiber controls)")
     ap.add_argument("--cross-iters", type=int, default=300)
@@ -431,6 +468,8 @@ def main():
         return run_crossing(args)
     if args.workload in ("bundle", "multi"):
         return run_calibrated(args)
+    if args.workload == "slabs":
+        return run_slabs(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
