@@ -83,6 +83,7 @@ struct prism_handle {
   std::vector<void*> allocs;
   // device buffers
   Tile* d_tiles = nullptr;
+  int32_t* d_tile_order = nullptr;   // the fused kernel's queue order (see tile_queue_order)
   GroupDev* d_groups = nullptr;
   float *d_y = nullptr, *d_theta = nullptr, *d_m = nullptr, *d_v = nullptr, *d_xf = nullptr;
   float *d_hsp = nullptr, *d_lp = nullptr, *d_gU = nullptr, *d_tile_ab = nullptr;
@@ -251,6 +252,7 @@ void fill_args(prism_handle* h) {
   a.Nmax = h->Nmax;
   a.G = h->G;
   a.tiles = h->d_tiles;
+  a.tile_order = h->d_tile_order;
   a.groups = h->d_groups;
   a.y = h->d_y;
   a.theta = h->d_theta;
@@ -408,6 +410,22 @@ static int32_t meas_order(const prism_volume& v, bool cal, std::vector<int32_t>&
   for (int n = 0; n < N; ++n)
     if (v.bvals[n] != 0.f) order.push_back(n);
   return nz / 2;
+}
+
+// Order in which the fused kernel's queue hands out tiles: every full tile in plan order
+// (volumes stay contiguous, so the measurement table rarely changes), then the partial tiles
+// by decreasing voxel count. The last tiles of an iteration are then the cheapest, which
+// shortens the tail where some CTAs are idle.
+static std::vector<int32_t> tile_queue_order(const std::vector<Tile>& tiles, int TV) {
+  std::vector<int32_t> order, part;
+  order.reserve(tiles.size());
+  for (size_t t = 0; t < tiles.size(); ++t) {
+    if (tiles[t].count == TV) order.push_back(static_cast<int32_t>(t));
+    else part.push_back(static_cast<int32_t>(t));
+  }
+  std::stable_sort(part.begin(), part.end(), [&](int32_t a, int32_t b) { return tiles[a].count > tiles[b].count; });
+  order.insert(order.end(), part.begin(), part.end());
+  return order;
 }
 
 struct Plan {
@@ -568,6 +586,7 @@ int init_impl(prism_handle* h, const prism_volume* vols, int n_vols, cudaStream_
   const int nce = (h->max_e + 255) / 256;
   // allocations
   RC(h->alloc(&h->d_tiles, h->ntiles));
+  RC(h->alloc(&h->d_tile_order, h->ntiles));
   RC(h->alloc(&h->d_groups, G));
   RC(h->alloc(&h->d_y, h->ypack_len));
   RC(h->alloc(&h->d_theta, static_cast<size_t>(Q) * Vp));
@@ -654,6 +673,7 @@ int init_impl(prism_handle* h, const prism_volume* vols, int n_vols, cudaStream_
   CK(cudaMemsetAsync(h->d_grad, 0, sizeof(float) * Q * static_cast<size_t>(Vp), st));
   // metadata
   RC(upload(h->d_tiles, h->tiles, st));
+  RC(upload(h->d_tile_order, tile_queue_order(h->tiles, h->TV), st));
   RC(upload(h->d_groups, h->groups, st));
   RC(upload(h->d_slot_of_vox, pl.slot_of_vox, st));
   RC(upload(h->d_slot_of_grid, pl.slot_of_grid, st));

@@ -72,6 +72,7 @@ struct IterArgs {
   int32_t Q, Vpad, TV, ntiles, Nmax, G;
   int32_t VW;              // voxels per warp slice of the packed signal (32 / threads per voxel)
   const Tile* tiles;
+  const int32_t* tile_order;   // queue position -> tile (full tiles first, partial ones by size)
   const GroupDev* groups;
   const float* y;          // packed b0-normalised signal
   float* theta;            // [Q][Vpad]

@@ -766,7 +766,8 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<K, TPV, LOSS,
     for (int w = 0; w < NW; ++w)
       for (int s = 0; s < kStages; ++s) mbar_init(&s_full[w][s], 1);
     fence_mbar_init();
-    s_first = atomicAdd(a.queue, 1);
+    const int q = atomicAdd(a.queue, 1);
+    s_first = (q < a.ntiles) ? a.tile_order[q] : a.ntiles;
   }
   __syncthreads();
   const float stepsz = a.adamc[0], isbc2 = a.adamc[1];
@@ -790,7 +791,10 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<K, TPV, LOSS,
   };
 
   while (t < a.ntiles) {
-    if (tid == 0) s_next = atomicAdd(a.queue, 1);
+    if (tid == 0) {
+      const int q = atomicAdd(a.queue, 1);
+      s_next = (q < a.ntiles) ? a.tile_order[q] : a.ntiles;
+    }
     __syncthreads();
     const int t_next = s_next;
     const Tile tl = a.tiles[t];
