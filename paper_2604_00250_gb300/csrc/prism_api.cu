@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <thread>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -412,6 +413,22 @@ static int32_t meas_order(const prism_volume& v, bool cal, std::vector<int32_t>&
   return nz / 2;
 }
 
+// Runs fn(begin, end) over [0, n) split into contiguous chunks on up to 16 host threads (one
+// chunk, on the calling thread, below `min_per_thread` items per thread).
+template <typename F>
+static void parallel_chunks(int64_t n, int64_t min_per_thread, F fn) {
+  unsigned hc = std::thread::hardware_concurrency();
+  int64_t nt = std::min<int64_t>(hc ? hc : 1, 16);
+  nt = std::max<int64_t>(1, std::min<int64_t>(nt, n / std::max<int64_t>(min_per_thread, 1)));
+  if (nt <= 1) {
+    fn(int64_t{0}, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (int64_t i = 0; i < nt; ++i) th.emplace_back(fn, n * i / nt, n * (i + 1) / nt);
+  for (auto& t : th) t.join();
+}
+
 // Order in which the fused kernel's queue hands out tiles: every full tile in plan order
 // (volumes stay contiguous, so the measurement table rarely changes), then the partial tiles
 // by decreasing voxel count. The last tiles of an iteration are then the cheapest, which
@@ -448,9 +465,26 @@ int build_plan(prism_handle* h, const prism_volume* vols, int n_vols, Plan& pl) 
     const prism_volume& v = vols[g];
     const int64_t ng = static_cast<int64_t>(v.nx) * v.ny * v.nz;
     vidx[g].assign(ng, -1);
-    int32_t c = 0;
-    for (int64_t i = 0; i < ng; ++i)
-      if (v.mask[i]) vidx[g][i] = c++;
+    // mask-order index of every masked grid position: chunk counts, then chunk offsets
+    constexpr int64_t kChunkN = 1 << 18;
+    const int64_t nch = (ng + kChunkN - 1) / kChunkN;
+    std::vector<int32_t> cc(nch + 1, 0);
+    parallel_chunks(nch, 4, [&](int64_t b, int64_t e) {
+      for (int64_t k = b; k < e; ++k) {
+        int32_t n = 0;
+        for (int64_t i = k * kChunkN; i < std::min(ng, (k + 1) * kChunkN); ++i) n += v.mask[i] != 0;
+        cc[k + 1] = n;
+      }
+    });
+    for (int64_t k = 0; k < nch; ++k) cc[k + 1] += cc[k];
+    parallel_chunks(nch, 4, [&](int64_t b, int64_t e) {
+      for (int64_t k = b; k < e; ++k) {
+        int32_t n = cc[k];
+        for (int64_t i = k * kChunkN; i < std::min(ng, (k + 1) * kChunkN); ++i)
+          if (v.mask[i]) vidx[g][i] = n++;
+      }
+    });
+    const int32_t c = cc[nch];
     if (c == 0) return fail(PRISM_E_SHAPE, "volume " + std::to_string(g) + ": empty mask");
     h->vox0[g] = Vtot;
     Vtot += c;
@@ -492,43 +526,69 @@ int build_plan(prism_handle* h, const prism_volume* vols, int n_vols, Plan& pl) 
     Nmax = std::max(Nmax, v.n_meas);
     gr.tile0 = static_cast<int32_t>(h->tiles.size());
     const int px = (v.nx + P - 1) / P, py = (v.ny + P - 1) / P, pz = (v.nz + P - 1) / P;
-    std::vector<int64_t> pv;
-    for (int a = 0; a < px; ++a)
-      for (int b = 0; b < py; ++b)
-        for (int c = 0; c < pz; ++c) {
-          pv.clear();
-          for (int x = a * P; x < std::min(v.nx, (a + 1) * P); ++x)
-            for (int y = b * P; y < std::min(v.ny, (b + 1) * P); ++y)
-              for (int z = c * P; z < std::min(v.nz, (c + 1) * P); ++z) {
-                const int64_t gi = (static_cast<int64_t>(x) * v.ny + y) * v.nz + z;
-                if (vidx[g][gi] >= 0) pv.push_back(gi);
-              }
-          if (pv.empty()) continue;
-          const int pid = static_cast<int>(h->patches.size());
-          const int tb = static_cast<int>(h->tiles.size());
-          for (size_t s0 = 0; s0 < pv.size(); s0 += TV) {
-            Tile t{};
-            t.group = g;
-            t.patch = pid;
-            t.slot0 = static_cast<int32_t>(h->tiles.size()) * TV;
-            t.count = static_cast<int32_t>(std::min<size_t>(TV, pv.size() - s0));
-            t.y_off = yoff;
-            t.ab_off = static_cast<int32_t>(aboff);
-            t.n_meas = v.n_meas;
-            yoff += static_cast<int64_t>((v.n_meas + 3) & ~3) * TV;
-            aboff += 2 * v.n_meas;
-            for (int i = 0; i < t.count; ++i) {
-              const int64_t gi = pv[s0 + i];
-              const int64_t vg = h->vox0[g] + vidx[g][gi];
-              const int slot = t.slot0 + i;
+    const int64_t npatch = static_cast<int64_t>(px) * py * pz;
+    // pass 1 (parallel): masked voxels per patch
+    std::vector<int32_t> pcount(npatch, 0);
+    auto patch_box = [&](int64_t pi, int lo[3], int hi[3]) {
+      const int a = static_cast<int>(pi / (static_cast<int64_t>(py) * pz)), b = static_cast<int>((pi / pz) % py),
+                c3 = static_cast<int>(pi % pz);
+      lo[0] = a * P, lo[1] = b * P, lo[2] = c3 * P;
+      hi[0] = std::min(v.nx, (a + 1) * P), hi[1] = std::min(v.ny, (b + 1) * P), hi[2] = std::min(v.nz, (c3 + 1) * P);
+    };
+    parallel_chunks(npatch, 16, [&](int64_t b0, int64_t e0) {
+      for (int64_t pi = b0; pi < e0; ++pi) {
+        int lo[3], hi[3];
+        patch_box(pi, lo, hi);
+        int32_t n = 0;
+        for (int x = lo[0]; x < hi[0]; ++x)
+          for (int y = lo[1]; y < hi[1]; ++y)
+            for (int z = lo[2]; z < hi[2]; ++z) n += vidx[g][(static_cast<int64_t>(x) * v.ny + y) * v.nz + z] >= 0;
+        pcount[pi] = n;
+      }
+    });
+    // tiles and patches in patch order (sequential, one entry per tile)
+    std::vector<int32_t> ptile(npatch, -1);
+    for (int64_t pi = 0; pi < npatch; ++pi) {
+      if (pcount[pi] == 0) continue;
+      const int pid = static_cast<int>(h->patches.size());
+      const int tb = static_cast<int>(h->tiles.size());
+      ptile[pi] = tb;
+      for (int32_t s0 = 0; s0 < pcount[pi]; s0 += TV) {
+        Tile t{};
+        t.group = g;
+        t.patch = pid;
+        t.slot0 = static_cast<int32_t>(h->tiles.size()) * TV;
+        t.count = std::min(TV, pcount[pi] - s0);
+        t.y_off = yoff;
+        t.ab_off = static_cast<int32_t>(aboff);
+        t.n_meas = v.n_meas;
+        yoff += static_cast<int64_t>((v.n_meas + 3) & ~3) * TV;
+        aboff += 2 * v.n_meas;
+        h->tiles.push_back(t);
+      }
+      h->patches.push_back({tb, static_cast<int>(h->tiles.size())});
+    }
+    // pass 2 (parallel): the slots of each patch's voxels, in C order within the patch
+    parallel_chunks(npatch, 16, [&](int64_t b0, int64_t e0) {
+      for (int64_t pi = b0; pi < e0; ++pi) {
+        if (ptile[pi] < 0) continue;
+        int lo[3], hi[3];
+        patch_box(pi, lo, hi);
+        int slot = ptile[pi] * TV;
+        for (int x = lo[0]; x < hi[0]; ++x)
+          for (int y = lo[1]; y < hi[1]; ++y)
+            for (int z = lo[2]; z < hi[2]; ++z) {
+              const int64_t gi = (static_cast<int64_t>(x) * v.ny + y) * v.nz + z;
+              const int32_t vi = vidx[g][gi];
+              if (vi < 0) continue;
+              const int64_t vg = h->vox0[g] + vi;
               pl.slot_of_vox[vg] = slot;
               pl.slot_of_grid[gr.grid_off + gi] = slot;
-              pl.row_off[vg] = h->yhat_off[g] + static_cast<int64_t>(vidx[g][gi]) * v.n_meas;
+              pl.row_off[vg] = h->yhat_off[g] + static_cast<int64_t>(vi) * v.n_meas;
+              ++slot;
             }
-            h->tiles.push_back(t);
-          }
-          h->patches.push_back({tb, static_cast<int>(h->tiles.size())});
-        }
+      }
+    });
     gr.ntiles = static_cast<int32_t>(h->tiles.size()) - gr.tile0;
   }
   h->ntiles = static_cast<int>(h->tiles.size());
@@ -788,7 +848,17 @@ int64_t count_voxels(const prism_volume* vols, int n) {
   int64_t V = 0;
   for (int g = 0; g < n; ++g) {
     const int64_t ng = static_cast<int64_t>(vols[g].nx) * vols[g].ny * vols[g].nz;
-    for (int64_t i = 0; i < ng; ++i) V += vols[g].mask[i] != 0;
+    constexpr int64_t kChunkN = 1 << 18;
+    const int64_t nch = (ng + kChunkN - 1) / kChunkN;
+    std::vector<int64_t> cc(nch, 0);
+    parallel_chunks(nch, 4, [&](int64_t b, int64_t e) {
+      for (int64_t k = b; k < e; ++k) {
+        int64_t c = 0;
+        for (int64_t i = k * kChunkN; i < std::min(ng, (k + 1) * kChunkN); ++i) c += vols[g].mask[i] != 0;
+        cc[k] = c;
+      }
+    });
+    for (int64_t c : cc) V += c;
   }
   return V;
 }
