@@ -93,13 +93,14 @@ def test_stitch_matches_oracle_on_given_parameters():
     f.close()
 
 
-@pytest.mark.parametrize("loss", ["mse", "nll"])
-def test_slab_fit_matches_oracle(loss):
-    """Ten fused iterations on every slab (each its own volume) and the stitched maps,
-    against the oracle's per-slab fits and stitching."""
+@pytest.mark.parametrize("loss,cal", [("mse", False), ("nll", False), ("nll", True)])
+def test_slab_fit_matches_oracle(loss, cal):
+    """Ten fused iterations on every slab (each its own volume, with its own sigma and, when
+    calibrated, its own bias field and per-measurement affine) and the stitched maps, against
+    the oracle's per-slab fits and stitching."""
     vol = _volume(1, shape=(4, 5, 17))
     slab, overlap = 7, 2
-    kw = dict(loss=loss, lam_sp=0.01, lam_dir=0.005)
+    kw = dict(loss=loss, calibration=cal, lam_sp=0.01, lam_dir=0.005)
     f = _fitter(vol, slab, overlap, **kw)
     ranges, parts = _slab_parts(vol, slab, overlap)
     th0 = f.params_host().astype(np.float64)
