@@ -302,6 +302,16 @@ def run_ours(args):
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{args.cpu_patches} fullest 16^3 patches ({nvox} voxels) x {args.cpu_iters} iterations, "
                          f"{dt:.1f} s"}
+        # the same oracle on one core (one patch, five iterations)
+        import torch
+        nt = torch.get_num_threads()
+        torch.set_num_threads(1)
+        try:
+            rate1, nvox1, dt1, _ = oracle_rate(vol, 1, 5)
+        finally:
+            torch.set_num_threads(nt)
+        cpu["value_1core"] = rate1
+        cpu["sample_1core"] = f"1 fullest 16^3 patch ({nvox1} voxels) x 5 iterations, {dt1:.1f} s"
     # per iteration: neighbour-prior preparation + fused kernel (groups finalised inside it)
     launches = (2 if PRIORS["lam_sp"] > 0 else 1)
     if rank == 0:
