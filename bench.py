@@ -420,6 +420,45 @@ def run_slabs(args):
     return 0
 
 
+def run_disco(args):
+    """The DiSCo1-shaped fit (Sec. 3 "Datasets" / "Configuration"): a 40^3 phantom of curved
+    bundles, 4 shells with b up to 13,192 s/mm^2 (4 b = 0 + 90 directions at 1000 / 3000 / 7000 /
+    13,192, N = 364), SNR 50, K = 5, Rician NLL with learned sigma, the topology and spatial
+    priors of Sec. 2.4, 300 iterations. Wall-clock time of the whole fit from pinned host
+    buffers."""
+    import types
+    import torch
+    import phantoms as P
+    import paper_2604_00250_gb300 as prism
+    sch = P.make_scheme(4, [(1000, 90), (3000, 90), (7000, 90), (13192, 90)], args.seed)
+    vol = P.bundle_phantom(args.seed, edge=40, snr=50.0, scheme=sch, device="cuda")
+    sig_host = torch.empty(tuple(vol.signal.shape), dtype=torch.float32, pin_memory=True)
+    sig_host.copy_(torch.as_tensor(vol.signal))
+    vh = types.SimpleNamespace(mask=vol.mask, signal=sig_host, bvals=vol.bvals, bvecs=vol.bvecs, init=None)
+    # the topology priors (repulsion, sparsity, orphan-WM, directional continuity, ordering)
+    # and the Huber-Laplacian smoothness, at the weights of Sec. 2.4
+    opts = prism.options(K=5, loss="nll", patch_dim=16, lam_orphan=0.01, lam_order=0.01, **PRIORS)
+    iters = 300
+    times = []
+    for rep in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        f = prism.Fitter(vh, opts)
+        f.step(iters)
+        th = f.params_host()
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+        prof = f.profile(20)
+        V = f.n_vox
+        f.close()
+    dt = min(times)
+    line = {"workload": "disco1_shaped_40cubed_N364_K5_nll_priors_300_iterations", "voxels": V, "iterations": iters,
+            "seconds": dt, "value": V * iters / dt, "unit": "voxel-iterations/s", "profile_ms": prof,
+            "timing": "wall clock, pinned host signal, set-up + iterations + read-out, best of 2"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_crossing(args):
     """Quality of the fit on the crossing-fiber benchmark layout (16 angles + single-fiber
     controls, N = 193) at each SNR and both data terms: one JSON line per run with the
@@ -466,10 +505,10 @@ def main():
     ap.add_argument("--no-unfused", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="brain", choices=["brain", "crossing", "bundle", "multi", "slabs"],
+    ap.add_argument("--workload", default="brain", choices=["brain", "crossing", "bundle", "multi", "slabs", "disco"],
                     help="crossing: fit quality on the crossing-fiber benchmark layout; bundle / multi: "
                          "speed of the calibrated NLL configurations; slabs: the whole-brain slab "
-                         "pipeline (not the headline)")
+                         "pipeline; disco: the DiSCo1-shaped K = 5 NLL fit (not the headline)")
     ap.add_argument("--cross-snr", type=float, nargs="+", default=[10.0, 30.0, 50.0])
     ap.add_argument("--cross-voxels", type=int, default=200, help="voxels per angle (and single-fiber controls)")
     ap.add_argument("--cross-iters", type=int, default=300)
@@ -480,6 +519,8 @@ def main():
         return run_calibrated(args)
     if args.workload == "slabs":
         return run_slabs(args)
+    if args.workload == "disco":
+        return run_disco(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

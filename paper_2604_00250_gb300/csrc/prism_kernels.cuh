@@ -292,24 +292,25 @@ __device__ __forceinline__ void acc_zero(Acc<K>& A) {
   A.l1 = A.l2 = A.l3 = A.u = 0.f;
 }
 
-template <int K, int TPV>
+// Sum of the accumulators over a voxel's TPV lanes, which lie STRIDE lanes apart.
+template <int K, int TPV, int STRIDE = 1>
 __device__ __forceinline__ void acc_reduce_tpv(Acc<K>& A) {
   if constexpr (TPV > 1) {
-    A.gS0 = warp_sum_range<1, TPV / 2>(A.gS0);
-    A.gcsf = warp_sum_range<1, TPV / 2>(A.gcsf);
-    A.ggm = warp_sum_range<1, TPV / 2>(A.ggm);
-    A.gres = warp_sum_range<1, TPV / 2>(A.gres);
+    A.gS0 = warp_sum_range<STRIDE, STRIDE * TPV / 2>(A.gS0);
+    A.gcsf = warp_sum_range<STRIDE, STRIDE * TPV / 2>(A.gcsf);
+    A.ggm = warp_sum_range<STRIDE, STRIDE * TPV / 2>(A.ggm);
+    A.gres = warp_sum_range<STRIDE, STRIDE * TPV / 2>(A.gres);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      A.gwa[k] = warp_sum_range<1, TPV / 2>(A.gwa[k]);
-      A.gwb[k] = warp_sum_range<1, TPV / 2>(A.gwb[k]);
+      A.gwa[k] = warp_sum_range<STRIDE, STRIDE * TPV / 2>(A.gwa[k]);
+      A.gwb[k] = warp_sum_range<STRIDE, STRIDE * TPV / 2>(A.gwb[k]);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) A.gd[k][c] = warp_sum_range<1, TPV / 2>(A.gd[k][c]);
+      for (int c = 0; c < 3; ++c) A.gd[k][c] = warp_sum_range<STRIDE, STRIDE * TPV / 2>(A.gd[k][c]);
     }
-    A.l1 = warp_sum_range<1, TPV / 2>(A.l1);
-    A.l2 = warp_sum_range<1, TPV / 2>(A.l2);
-    A.l3 = warp_sum_range<1, TPV / 2>(A.l3);
-    A.u = warp_sum_range<1, TPV / 2>(A.u);
+    A.l1 = warp_sum_range<STRIDE, STRIDE * TPV / 2>(A.l1);
+    A.l2 = warp_sum_range<STRIDE, STRIDE * TPV / 2>(A.l2);
+    A.l3 = warp_sum_range<STRIDE, STRIDE * TPV / 2>(A.l3);
+    A.u = warp_sum_range<STRIDE, STRIDE * TPV / 2>(A.u);
   }
 }
 
@@ -585,6 +586,77 @@ __device__ __forceinline__ void accp_fold(const Vox<K>& P, const AccP<K>& B, Acc
   A.gS0 = g;
 }
 
+// The packed accumulators' sums (accp_fold without the S0 term, which needs the voxel's
+// transform): for several lanes per voxel, whose sums are combined before the transform.
+template <int K, int LOSS, bool CAL>
+__device__ __forceinline__ void accp_sums(const AccP<K>& B, Acc<K>& A) {
+  A.gS0 = 0.f;
+  A.gcsf = -(B.gcsf.x + B.gcsf.y);
+  A.ggm = -(B.ggm.x + B.ggm.y);
+  A.gres = -(B.gres.x + B.gres.y);
+  A.l1 = B.l1.x + B.l1.y;
+  if constexpr (LOSS == kLossNLL) {
+    A.l2 = B.l2;
+    A.l3 = B.l3;
+  }
+  if constexpr (CAL) A.u = -(B.u.x + B.u.y);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    A.gwa[k] = -(B.gwa[k].x + B.gwa[k].y);
+    A.gwb[k] = -(B.gwb[k].x + B.gwb[k].y);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) A.gd[k][c] = -(B.gd[k][c].x + B.gd[k][c].y);
+  }
+}
+
+// sum_n q_n T_n from the per-compartment sums (T = sum of fraction-weighted compartment signals).
+template <int K>
+__device__ __forceinline__ float acc_gS0(const Vox<K>& P, const Acc<K>& A) {
+  float g = P.f[0] * A.gcsf + P.f[1] * A.ggm + P.f[K + 2] * A.gres;
+#pragma unroll
+  for (int k = 0; k < K; ++k) g = fmaf(P.f[2 + k] * P.fin, A.gwa[k], fmaf(P.f[2 + k] * P.omf, A.gwb[k], g));
+  return g;
+}
+
+// Accumulators of a tile's voxels in shared memory, field-major: s[f * TV + v], 8 + 5K fields.
+template <int K>
+__device__ __forceinline__ void acc_put(const Acc<K>& A, float* s, int TV, int v) {
+  s[0 * TV + v] = A.gS0;
+  s[1 * TV + v] = A.gcsf;
+  s[2 * TV + v] = A.ggm;
+  s[3 * TV + v] = A.gres;
+  s[4 * TV + v] = A.l1;
+  s[5 * TV + v] = A.l2;
+  s[6 * TV + v] = A.l3;
+  s[7 * TV + v] = A.u;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    s[(8 + 5 * k) * TV + v] = A.gwa[k];
+    s[(9 + 5 * k) * TV + v] = A.gwb[k];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) s[(10 + 5 * k + c) * TV + v] = A.gd[k][c];
+  }
+}
+
+template <int K>
+__device__ __forceinline__ void acc_get(Acc<K>& A, const float* s, int TV, int v) {
+  A.gS0 = s[0 * TV + v];
+  A.gcsf = s[1 * TV + v];
+  A.ggm = s[2 * TV + v];
+  A.gres = s[3 * TV + v];
+  A.l1 = s[4 * TV + v];
+  A.l2 = s[5 * TV + v];
+  A.l3 = s[6 * TV + v];
+  A.u = s[7 * TV + v];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    A.gwa[k] = s[(8 + 5 * k) * TV + v];
+    A.gwb[k] = s[(9 + 5 * k) * TV + v];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) A.gd[k][c] = s[(10 + 5 * k + c) * TV + v];
+  }
+}
+
 // Scaled data-term gradient w.r.t. transformed parameters.
 template <int K>
 __device__ __forceinline__ void data_grad(const Vox<K>& P, const Acc<K>& A, float scale, float& gS0,
@@ -636,7 +708,7 @@ __device__ __forceinline__ void block_reduce3(double v0, double v1, double v2, d
 // calibration, data term, adjoint, priors, chain rule and the voxel Adam update.
 //
 // Each warp streams the signal of its own VW voxels (a contiguous [NP][VW] slice of
-// the tile's packed block) through a private ring of kStages shared-memory buffers of
+// the tile's packed block) through a private ring of NS shared-memory buffers of
 // kChunk measurements, refilled by its lane 0 with bulk TMA copies (cp.async.bulk)
 // tracked by per-stage mbarriers. The stream runs across tile boundaries: while a
 // warp finishes a tile it already fetches the first chunks of the CTA's next tile.
@@ -724,12 +796,21 @@ __device__ __forceinline__ void finalize_groups(const IterArgs& a, double (*s_su
   }
 }
 
+// Whether the fused kernel takes two measurements per step in f32x2 arithmetic. One thread
+// per voxel: all but the calibrated NLL with five fibers (its packed form spills even at 170
+// registers and measured 11 % slower). Four lanes per voxel: without calibration. Sixteen
+// lanes per voxel (one pair per lane and chunk): never, the scalar loop measured 0-20 % faster.
+template <int K, int TPV, int LOSS, bool CAL>
+__host__ __device__ constexpr bool fused_packed() {
+  return (TPV == 1) ? !(CAL && LOSS == kLossNLL && K >= 5) : (TPV == 4 && !CAL);
+}
+
 // CTAs per SM the fused kernel is compiled for: 4 (128 registers per thread) where the voxel
-// state fits, 3 (170 registers) for five fibers and for the packed NLL / calibrated variants,
-// which spill at 128 and measured 7-54 % faster at 3.
+// state fits, 3 (170 registers) for five fibers, the packed NLL and the calibrated variants
+// with one thread per voxel, which spill at 128 and measured 7-54 % faster at 3.
 template <int K, int TPV, int LOSS, bool CAL>
 constexpr int fused_min_blocks() {
-  return ((K >= 5) || (TPV == 1 && (LOSS == kLossNLL || CAL))) ? 3 : 4;
+  return ((K >= 5) || (TPV == 1 && CAL) || (fused_packed<K, TPV, LOSS, CAL>() && LOSS == kLossNLL)) ? 3 : 4;
 }
 
 template <int K, int TPV, int LOSS, bool CAL>
@@ -737,34 +818,40 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<K, TPV, LOSS,
   constexpr int NF = K + 3, Q = 4 * K + 5, XF = 4 * K + 3;
   constexpr int NW = kFusedThreads / 32;
   constexpr int VW = 32 / TPV;              // voxels per warp
-  // packed two-measurement steps with one thread per voxel; the calibrated NLL with five
-  // fibers keeps the scalar loop (its packed form spills even at 170 registers and measured
-  // 11 % slower)
-  constexpr bool PACKED = (TPV == 1) && !(CAL && LOSS == kLossNLL && K >= 5);
-  constexpr bool HOIST = PACKED && K <= 3 && LOSS == kLossMSE && !CAL;
+  constexpr bool PACKED = fused_packed<K, TPV, LOSS, CAL>();
+  constexpr bool HOIST = PACKED && TPV == 1 && K <= 3 && LOSS == kLossMSE && !CAL;
+  // ring stages per warp (kStages; a ring as deep in bytes for four or sixteen lanes per voxel,
+  // kStages * TPV, measured 0-25 % slower)
+  constexpr int NS = kStages;
   static_assert(kChunk % TPV == 0, "chunk must split evenly across the voxel's lanes");
   extern __shared__ __align__(16) unsigned char smem[];
   const int Vp = a.Vpad;
   MeasRow* s_tab = reinterpret_cast<MeasRow*>(smem);
-  float* s_ring = reinterpret_cast<float*>(s_tab + a.Nmax);                 // [NW][kStages][kChunk][VW]
-  float* s_blr = s_ring + NW * kStages * kChunk * VW;                       // [512] (calibration)
+  float* s_ring = reinterpret_cast<float*>(s_tab + a.Nmax);                 // [NW][NS][kChunk][VW]
+  float* s_blr = s_ring + NW * NS * kChunk * VW;                       // [512] (calibration)
   float* s_ab = s_blr + (CAL ? kNGrid : 0);                                 // [NW][2][Nmax] (calibration)
   __shared__ uint64_t s_bar;                 // table / bias grid
-  __shared__ uint64_t s_full[NW][kStages];
+  __shared__ uint64_t s_full[NW][NS];
   __shared__ int s_first, s_next;
   __shared__ double s_red[8][3];
+  // several lanes per voxel: the tile's reduced accumulators, handed to the epilogue threads
+  constexpr int TV = kFusedThreads / TPV;
+  __shared__ float s_acc[(TPV > 1) ? (8 + 5 * K) * TV : 1];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int vl = tid / TPV, js = tid % TPV, lv = lane / TPV;
+  // A voxel's TPV lanes lie VW apart (lane = js * VW + lv): the lanes that read one table row
+  // at a time are then contiguous, so table reads stay broadcasts and signal reads contiguous.
+  const int lv = (TPV == 1) ? lane : lane % VW, js = (TPV == 1) ? 0 : lane / VW;
+  const int vl = (TPV == 1) ? tid : warp * VW + lv;
   const int step = *a.step;
   const int par = step & 1;
   const float* xf_cur = a.xf + static_cast<size_t>(par) * XF * Vp;
   float* xf_nxt = a.xf + static_cast<size_t>(par ^ 1) * XF * Vp;
-  float* ring = s_ring + warp * (kStages * kChunk * VW);
+  float* ring = s_ring + warp * (NS * kChunk * VW);
   if (tid == 0) {
     mbar_init(&s_bar, 1);
     for (int w = 0; w < NW; ++w)
-      for (int s = 0; s < kStages; ++s) mbar_init(&s_full[w][s], 1);
+      for (int s = 0; s < NS; ++s) mbar_init(&s_full[w][s], 1);
     fence_mbar_init();
     const int q = atomicAdd(a.queue, 1);
     s_first = (q < a.ntiles) ? a.tile_order[q] : a.ntiles;
@@ -781,7 +868,7 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<K, TPV, LOSS,
 
   // Lane 0: issue stream position `pos` = chunk j of the tile at y_off (NP padded rows).
   auto issue = [&](uint32_t pos, int64_t y_off, int NP, int j) {
-    const int s = pos % kStages;
+    const int s = pos % NS;
     const int cnt = min(kChunk, NP - j * kChunk);
     const uint32_t bytes = static_cast<uint32_t>(cnt) * VW * 4u;
     const float* src = a.y + y_off + static_cast<int64_t>(warp) * NP * VW + static_cast<int64_t>(j) * kChunk * VW;
@@ -881,8 +968,8 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<K, TPV, LOSS,
     if constexpr (PACKED) voxp_init<K>(P, DP, AP);
     for (int j = 0; j < nch; ++j) {
       if (lane == 0) {
-        // keep kStages chunks of this warp's stream in flight (this tile, then the next)
-        while (iss < g + kStages) {
+        // keep NS chunks of this warp's stream in flight (this tile, then the next)
+        while (iss < g + NS) {
           const uint32_t r = iss - base;
           if (r < static_cast<uint32_t>(nch)) issue(iss, tl.y_off, NP, r);
           else if (r - nch < static_cast<uint32_t>(nnch)) issue(iss, ny_off, nNP, r - nch);
@@ -890,8 +977,8 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<K, TPV, LOSS,
           ++iss;
         }
       }
-      const int s = g % kStages;
-      if (!failed && !mbar_wait(&s_full[warp][s], (g / kStages) & 1)) {
+      const int s = g % NS;
+      if (!failed && !mbar_wait(&s_full[warp][s], (g / NS) & 1)) {
         atomicOr(a.status, kStTimeout);
         failed = true;
       }
@@ -930,15 +1017,25 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<K, TPV, LOSS,
             }
           }
         } else if (act && cnt == kChunk && i0 == 0) {
+          // lane js of the voxel takes pairs js, js + TPV, ...
           // (with five fibers unrolling spills: one step at a time measured 2-6 % faster)
 #pragma unroll (K >= 5 ? 1 : 2)
-          for (int i = 0; i < kChunk / 2; ++i)
-            step2<K, false, LOSS>(DP, tab2[i], yc2[i * VW], make_float2(1.f, 1.f), AP, inv_s2);
-        } else if (act) {
+          for (int i = 0; i < kChunk / 2 / TPV; ++i) {
+            const int pi = (TPV == 1) ? i : i * TPV + js;
+            step2<K, false, LOSS>(DP, tab2[pi], yc2[pi * VW], make_float2(1.f, 1.f), AP, inv_s2);
+          }
+        } else if (act && TPV == 1) {
           if (i0 > 0) step2_b0<K>(DP, yc2, VW, i0, AP);
 #pragma unroll 1
           for (int i = i0; i < (cnt + 1) / 2; ++i)
             step2<K, true, LOSS>(DP, tab2[i], yc2[i * VW], make_float2(1.f, (2 * i + 1 < cnt) ? 1.f : 0.f), AP,
+                                 inv_s2);
+        } else if (act) {
+          if (i0 > js) step2_b0<K>(DP, yc2 + js * VW, TPV * VW, (i0 - js + TPV - 1) / TPV, AP);
+          const int first = i0 + ((js - i0) % TPV + TPV) % TPV;   // this lane's first pair >= i0
+#pragma unroll 1
+          for (int pi = first; pi < (cnt + 1) / 2; pi += TPV)
+            step2<K, true, LOSS>(DP, tab2[pi], yc2[pi * VW], make_float2(1.f, (2 * pi + 1 < cnt) ? 1.f : 0.f), AP,
                                  inv_s2);
         }
         __syncwarp();
@@ -988,9 +1085,10 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<K, TPV, LOSS,
           float rr = 0.f, u = 0.f;
           if (ok) pair<K, LOSS, CAL, false>(P, ffin, fomf, tab[nl], yc[(nl >> 1) * (2 * VW) + (nl & 1)], B, inv_s2, 0.f, A, rr, u);
           if (CAL) {
-            float su = warp_sum_range<TPV, 16>(ok ? u : 0.f);
-            float sr = warp_sum_range<TPV, 16>(ok ? rr : 0.f);
-            if (lane < TPV && nl < cnt) {
+            // over the warp's voxels: the VW lanes of one js are contiguous
+            float su = warp_sum_range<1, VW / 2>(ok ? u : 0.f);
+            float sr = warp_sum_range<1, VW / 2>(ok ? rr : 0.f);
+            if (lv == 0 && nl < cnt) {
               s_ab[(warp * 2) * a.Nmax + j * kChunk + nl] = su;
               s_ab[(warp * 2 + 1) * a.Nmax + j * kChunk + nl] = sr;
             }
@@ -1001,68 +1099,91 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<K, TPV, LOSS,
       ++g;
     }
     base += nch;
-    // voxel transforms again (not kept live across the loop). Where registers allow (HOIST),
-    // the raw parameters and the moments are read here, once, so that their latency overlaps
-    // the epilogue's math; otherwise they are re-read before the update.
-    const bool writer = act && (js == 0);
-    float th[Q], mq[Q], vq[Q];
-    load_theta<K>(a.theta, Vp, slot, act, th);
-    if constexpr (HOIST) load_moments<Q>(a, slot, writer, mq, vq);
-    transform<K>(th, P);
-    if constexpr (PACKED) accp_fold<K, LOSS, CAL>(P, AP, A);
-    acc_reduce_tpv<K, TPV>(A);
+    if constexpr (TPV > 1) {
+      // sum each voxel's lanes and hand the sums to one epilogue thread: voxel v of the tile
+      // goes to thread v, so that a warp's epilogue serves 32 voxels, as with one thread per voxel
+      if constexpr (PACKED) accp_sums<K, LOSS, CAL>(AP, A);
+      acc_reduce_tpv<K, TPV, VW>(A);
+      if (js == 0) acc_put<K>(A, s_acc, TV, vl);
+      __syncthreads();
+    }
+    // the epilogue's voxel: the thread's own with one thread per voxel, else voxel tid of the
+    // tile for the first TV threads (the others skip to the tile partials)
+    const bool epi = (TPV == 1) || tid < TV;
+    const int eslot = (TPV == 1) ? slot : tl.slot0 + min(tid, TV - 1);
+    const bool eact = (TPV == 1) ? act : (tid < tl.count);
+    const bool writer = eact && (js == 0 || TPV > 1);
+    float dloss = 0.f, dsig = 0.f, ploss = 0.f;
+    if (epi) {
+      // voxel transforms again (not kept live across the loop). Where registers allow (HOIST),
+      // the raw parameters and the moments are read here, once, so that their latency overlaps
+      // the epilogue's math; otherwise they are re-read before the update.
+      float th[Q], mq[Q], vq[Q];
+      load_theta<K>(a.theta, Vp, eslot, eact, th);
+      if constexpr (HOIST) load_moments<Q>(a, eslot, writer, mq, vq);
+      transform<K>(th, P);
+      if constexpr (TPV == 1) {
+        if constexpr (PACKED) accp_fold<K, LOSS, CAL>(P, AP, A);
+      } else {
+        acc_get<K>(A, s_acc, TV, tid);
+        if constexpr (PACKED) A.gS0 = acc_gS0<K>(P, A);
+        if constexpr (CAL) {
+          unpack_coord(eact ? a.vcoord[eslot] : 0u, cx, cy, cz);
+          B = expf(tri_eval(s_blr, tri_weights(cx, cy, cz, gr.nx, gr.ny, gr.nz)));
+        }
+      }
 
-    // ---- data-term gradient and value
-    float gS0, gf[NF], gd[K][3], gfin;
-    data_grad<K>(P, A, scale, gS0, gf, gd, gfin);
-    float dloss, dsig = 0.f;
-    if (LOSS == kLossMSE) {
-      dloss = A.l1 * gr.inv_M;
-    } else {
-      dloss = 2.f * slog * N + 0.5f * inv_s2 * A.l1 - A.l3;
-      dsig = 2.f * N - inv_s2 * (A.l1 + 2.f * A.l2);
-    }
-    // ---- priors
-    float ploss = priors<K>(a, P, slot, gr.inv_M, xf_cur, gS0, gf, gd);
-    float gUv = A.u * scale;
-    if (CAL && a.w_tv > 0.f) {
-      const uint32_t fl = act ? a.vflag[slot] : 0u;
-      ploss += tv_term(s_blr, cx, cy, cz, gr, fl, B, a.w_tv * gr.inv_M, a.tv_eps, gUv);
-    }
-    // ---- chain rule and the update
-    if constexpr (!HOIST) {
-      load_theta<K>(a.theta, Vp, slot, act, th);
-      load_moments<Q>(a, slot, writer, mq, vq);
-    }
-    float gq[Q];
-    chain_raw<K>(P, gS0, gf, gd, gfin, gq);
-    if (a.optimizer == 0) {
-#pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        mq[q] = fmaf(a.beta1, mq[q], (1.f - a.beta1) * gq[q]);
-        vq[q] = fmaf(a.beta2, vq[q], (1.f - a.beta2) * gq[q] * gq[q]);
-        th[q] -= stepsz * mq[q] * frcp(fmaf(fsqrt(vq[q]), isbc2, a.eps));
+      // ---- data-term gradient and value
+      float gS0, gf[NF], gd[K][3], gfin;
+      data_grad<K>(P, A, scale, gS0, gf, gd, gfin);
+      if (LOSS == kLossMSE) {
+        dloss = A.l1 * gr.inv_M;
+      } else {
+        dloss = 2.f * slog * N + 0.5f * inv_s2 * A.l1 - A.l3;
+        dsig = 2.f * N - inv_s2 * (A.l1 + 2.f * A.l2);
       }
-    } else {
-#pragma unroll
-      for (int q = 0; q < Q; ++q)
-        rprop_update(th[q], mq[q], vq[q], gq[q], a.lr, a.eta_minus, a.eta_plus, a.step_min, a.step_max);
-    }
-    if (writer) {
-#pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        const size_t ix = static_cast<size_t>(q) * Vp + slot;
-        a.m[ix] = mq[q];
-        a.v[ix] = vq[q];
-        a.theta[ix] = th[q];
+      // ---- priors
+      ploss = priors<K>(a, P, eslot, gr.inv_M, xf_cur, gS0, gf, gd);
+      float gUv = A.u * scale;
+      if (CAL && a.w_tv > 0.f) {
+        const uint32_t fl = eact ? a.vflag[eslot] : 0u;
+        ploss += tv_term(s_blr, cx, cy, cz, gr, fl, B, a.w_tv * gr.inv_M, a.tv_eps, gUv);
       }
+      // ---- chain rule and the update
+      if constexpr (!HOIST) {
+        load_theta<K>(a.theta, Vp, eslot, eact, th);
+        load_moments<Q>(a, eslot, writer, mq, vq);
+      }
+      float gq[Q];
+      chain_raw<K>(P, gS0, gf, gd, gfin, gq);
+      if (a.optimizer == 0) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          mq[q] = fmaf(a.beta1, mq[q], (1.f - a.beta1) * gq[q]);
+          vq[q] = fmaf(a.beta2, vq[q], (1.f - a.beta2) * gq[q] * gq[q]);
+          th[q] -= stepsz * mq[q] * frcp(fmaf(fsqrt(vq[q]), isbc2, a.eps));
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+          rprop_update(th[q], mq[q], vq[q], gq[q], a.lr, a.eta_minus, a.eta_plus, a.step_min, a.step_max);
+      }
+      if (writer) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          const size_t ix = static_cast<size_t>(q) * Vp + eslot;
+          a.m[ix] = mq[q];
+          a.v[ix] = vq[q];
+          a.theta[ix] = th[q];
+        }
+      }
+      if (a.nb_priors && writer) {
+        Vox<K> Pn;
+        transform<K>(th, Pn);
+        store_xf<K>(xf_nxt, Vp, eslot, Pn);
+      }
+      if (CAL && writer) a.gU[eslot] = gUv;
     }
-    if (a.nb_priors && writer) {
-      Vox<K> Pn;
-      transform<K>(th, Pn);
-      store_xf<K>(xf_nxt, Vp, slot, Pn);
-    }
-    if (CAL && writer) a.gU[slot] = gUv;
     // ---- tile partials (fixed-order reductions)
     block_reduce3(writer ? static_cast<double>(dloss) : 0.0, writer ? static_cast<double>(dsig) : 0.0,
                   writer ? static_cast<double>(ploss) : 0.0, s_red, a.tile_red + 4 * static_cast<size_t>(t));
@@ -1080,7 +1201,7 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<K, TPV, LOSS,
   }
   if (failed && lane == 0) {
     // let copies still in flight land before the CTA's shared memory is released
-    for (uint32_t p = g; p < iss; ++p) mbar_wait(&s_full[warp][p % kStages], (p / kStages) & 1);
+    for (uint32_t p = g; p < iss; ++p) mbar_wait(&s_full[warp][p % NS], (p / NS) & 1);
   }
   // The last CTA to leave resets the queue for the next iteration (and, without
   // calibration, finalises the groups).
