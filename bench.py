@@ -284,16 +284,22 @@ def run_ours(args):
         keep = []
         arr, nv = prism._volumes_array([vhost], keep)
         loss_out = np.empty(1, dtype=np.float64)
-        barrier()
-        t0 = time.perf_counter()
-        _lib.check(lib.prism_fit(arr, nv, ctypes.byref(opts), n_e2e, ctypes.c_void_p(out.data_ptr()),
-                                 loss_out.ctypes.data, prism.MEM_HOST, ctypes.c_void_p(stream.cuda_stream)))
-        torch.cuda.synchronize()
-        dt = max_over_ranks(time.perf_counter() - t0)
+        # three complete calls, the fastest reported and all listed: on the shared GB300 hosts
+        # the wall time of a call varies by up to 12 % (the device time of its iterations does not)
+        runs = []
+        for _ in range(3):
+            barrier()
+            t0 = time.perf_counter()
+            _lib.check(lib.prism_fit(arr, nv, ctypes.byref(opts), n_e2e, ctypes.c_void_p(out.data_ptr()),
+                                     loss_out.ctypes.data, prism.MEM_HOST, ctypes.c_void_p(stream.cuda_stream)))
+            torch.cuda.synchronize()
+            runs.append(max_over_ranks(time.perf_counter() - t0))
+        dt = min(runs)
         h2d = sig_host.numel() * 4 + vol.mask.size + N * 16
         d2h = out.numel() * 4 + 8
         e2e = {"value": world * V * n_e2e / dt, "unit": UNIT, "h2d_bytes_per_step": h2d / n_e2e,
                "d2h_bytes_per_step": d2h / n_e2e, "iterations": n_e2e, "seconds": dt,
+               "seconds_all_calls": [round(r, 4) for r in runs], "timing": "wall clock, fastest of 3 calls",
                "call": "prism_fit (init + iterations + readout), pinned host signal and parameters"}
     # ---- CPU baseline: the FP64 oracle on a bounded sample (rank 0, N = 1 only)
     cpu = None

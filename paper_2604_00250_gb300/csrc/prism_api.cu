@@ -620,7 +620,8 @@ int upload(T* dst, const std::vector<T>& src, cudaStream_t st) {
     if (r_ != PRISM_OK) return r_; \
   } while (0)
 
-int init_impl(prism_handle* h, const prism_volume* vols, int n_vols, cudaStream_t st) {
+int init_impl(prism_handle* h, const prism_volume* vols, int n_vols, const std::vector<int64_t>& counts,
+              cudaStream_t st) {
   const prism_options& o = h->opt;
   h->K = o.K;
   h->Q = 4 * o.K + 5;
@@ -629,6 +630,25 @@ int init_impl(prism_handle* h, const prism_volume* vols, int n_vols, cudaStream_
   h->nb = (o.lam_sp > 0.f) || (o.lam_dir > 0.f);
   h->ks = &kernels_for_k(o.K);
   h->TV = h->NT / h->TPV;
+  // Host signals start their copy to the device before the plan is built: a copy needs only the
+  // voxel count, and the DMA then runs while the host builds the plan. All copies start at once
+  // when together they take at most a quarter of the free device memory; otherwise each volume
+  // is copied in turn below.
+  std::vector<float*> early(n_vols, nullptr);
+  {
+    size_t bytes = 0;
+    for (int g = 0; g < n_vols; ++g)
+      if (vols[g].mem == PRISM_MEM_HOST) bytes += sizeof(float) * static_cast<size_t>(counts[g]) * vols[g].n_meas;
+    size_t fr = 0, tot = 0;
+    if (bytes > 0 && cudaMemGetInfo(&fr, &tot) == cudaSuccess && bytes <= fr / 4) {
+      for (int g = 0; g < n_vols; ++g) {
+        if (vols[g].mem != PRISM_MEM_HOST) continue;
+        const size_t n = static_cast<size_t>(counts[g]) * vols[g].n_meas;
+        RC(h->alloc(&early[g], n));
+        CK(cudaMemcpyAsync(early[g], vols[g].signal, sizeof(float) * n, cudaMemcpyHostToDevice, st));
+      }
+    }
+  }
   Plan pl;
   RC(build_plan(h, vols, n_vols, pl));
   const int Vp = h->Vpad, Q = h->Q, G = h->G;
@@ -753,8 +773,10 @@ int init_impl(prism_handle* h, const prism_volume* vols, int n_vols, cudaStream_
     const int N = v.n_meas;
     const int64_t Vg = gr.n_vox;
     const float* sig = v.signal;
-    float* tmp_sig = nullptr;
-    if (v.mem == PRISM_MEM_HOST) {
+    float* tmp_sig = early[g];
+    if (tmp_sig) {
+      sig = tmp_sig;
+    } else if (v.mem == PRISM_MEM_HOST) {
       RC(h->alloc(&tmp_sig, static_cast<size_t>(Vg) * N));
       CK(cudaMemcpyAsync(tmp_sig, v.signal, sizeof(float) * Vg * N, cudaMemcpyHostToDevice, st));
       sig = tmp_sig;
@@ -846,8 +868,9 @@ int choose_shape(const prism_options& o, int64_t V, int* tpv, int* nt) {
   return PRISM_OK;
 }
 
-int64_t count_voxels(const prism_volume* vols, int n) {
-  int64_t V = 0;
+// Masked voxels of each volume.
+std::vector<int64_t> count_voxels(const prism_volume* vols, int n) {
+  std::vector<int64_t> V(n, 0);
   for (int g = 0; g < n; ++g) {
     const int64_t ng = static_cast<int64_t>(vols[g].nx) * vols[g].ny * vols[g].nz;
     constexpr int64_t kChunkN = 1 << 18;
@@ -860,7 +883,7 @@ int64_t count_voxels(const prism_volume* vols, int n) {
         cc[k] = c;
       }
     });
-    for (int64_t c : cc) V += c;
+    for (int64_t c : cc) V[g] += c;
   }
   return V;
 }
@@ -872,14 +895,14 @@ int build_graphs(prism_handle* h) {
   return PRISM_OK;
 }
 
-int create_handle(const prism_volume* vols, int n_vols, const prism_options& o, int tpv, int nt,
-                  cudaStream_t st, prism_handle** out) {
+int create_handle(const prism_volume* vols, int n_vols, const std::vector<int64_t>& counts, const prism_options& o,
+                  int tpv, int nt, cudaStream_t st, prism_handle** out) {
   std::unique_ptr<prism_handle> h(new (std::nothrow) prism_handle());
   if (!h) return fail(PRISM_E_OOM, "host allocation failed");
   h->opt = o;
   h->TPV = tpv;
   h->NT = nt;
-  RC(init_impl(h.get(), vols, n_vols, st));
+  RC(init_impl(h.get(), vols, n_vols, counts, st));
   if (o.fused && o.use_graph) RC(build_graphs(h.get()));
   *out = h.release();
   return PRISM_OK;
@@ -899,7 +922,9 @@ extern "C" int prism_fit_init(const prism_volume* vols, int32_t n_vols, const pr
   RC(validate_options(o));
   for (int g = 0; g < n_vols; ++g) RC(validate_volume(vols[g], g));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int64_t V = count_voxels(vols, n_vols);
+  const std::vector<int64_t> counts = count_voxels(vols, n_vols);
+  int64_t V = 0;
+  for (int64_t c : counts) V += c;
   int tpv = 1, nt = 128;
   choose_shape(o, V, &tpv, &nt);
   if (o.autotune && o.fused) {
@@ -915,7 +940,7 @@ extern "C" int prism_fit_init(const prism_volume* vols, int32_t n_vols, const pr
     for (const auto& c : cands) {
       if (o.threads_per_voxel && c[0] != o.threads_per_voxel) continue;
       prism_handle* hc = nullptr;
-      if (create_handle(vols, n_vols, oc, c[0], c[1], st, &hc) != PRISM_OK) {
+      if (create_handle(vols, n_vols, counts, oc, c[0], c[1], st, &hc) != PRISM_OK) {
         g_err.clear();
         continue;
       }
@@ -938,7 +963,7 @@ extern "C" int prism_fit_init(const prism_volume* vols, int32_t n_vols, const pr
     g_err.clear();
   }
   prism_handle* h = nullptr;
-  const int rc = create_handle(vols, n_vols, o, tpv, nt, st, &h);
+  const int rc = create_handle(vols, n_vols, counts, o, tpv, nt, st, &h);
   if (rc != PRISM_OK) return rc;
   *out = h;
   return PRISM_OK;
