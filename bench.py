@@ -41,9 +41,9 @@ FLOPS_PER_PAIR = 17 + 28 * K_FIB
 # r = y - S0 sum(f) and r^2 (two multiply-adds) and the running sum of r (one add).
 FLOPS_PER_B0_PAIR = 5
 # DRAM bytes per voxel-iteration of the fused kernel (read + write), from an ncu capture of
-# this kernel version on the scaled brain (212,900 voxels: 394.9 MB per launch); traffic grows
+# this kernel version on the scaled brain (212,900 voxels: 396.0 and 392.1 MB in two launches); traffic grows
 # in proportion to the voxels. Must return to None when the kernel changes.
-TRAFFIC_BYTES_PER_VOXEL_ITER = 1854.9
+TRAFFIC_BYTES_PER_VOXEL_ITER = 1851.0
 # FP32 peak: 152 SMs x 128 lanes x 2 flops x 2070 MHz (maximum SM clock).
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
