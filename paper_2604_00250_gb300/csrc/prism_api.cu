@@ -87,7 +87,7 @@ struct prism_handle {
   int32_t* d_tile_order = nullptr;   // the fused kernel's queue order (see tile_queue_order)
   GroupDev* d_groups = nullptr;
   float *d_y = nullptr, *d_theta = nullptr, *d_m = nullptr, *d_v = nullptr, *d_xf = nullptr;
-  float *d_hsp = nullptr, *d_lp = nullptr, *d_gU = nullptr, *d_tile_ab = nullptr;
+  float *d_hsp = nullptr, *d_lp = nullptr, *d_pg = nullptr, *d_gU = nullptr, *d_tile_ab = nullptr;
   float *d_gparams = nullptr, *d_gm = nullptr, *d_gv = nullptr;
   float *d_yhat = nullptr, *d_r = nullptr, *d_grad = nullptr;
   int32_t *d_nbr = nullptr, *d_queue = nullptr, *d_done = nullptr, *d_step = nullptr, *d_status = nullptr;
@@ -262,6 +262,7 @@ void fill_args(prism_handle* h) {
   a.xf = h->d_xf;
   a.hsp = h->d_hsp;
   a.lp = h->d_lp;
+  a.pg = h->d_pg;
   a.nbr = h->d_nbr;
   a.vcoord = h->d_vcoord;
   a.vflag = h->d_vflag;
@@ -343,6 +344,7 @@ void fill_args(prism_handle* h) {
 int enqueue_fused_iter(prism_handle* h, cudaStream_t st) {
   const IterArgs& a = h->ia;
   if (h->opt.lam_sp > 0.f) CK(h->ks->prior_prep(a, 0, h->ntiles, st));
+  if (h->nb && h->TPV > 1) CK(h->ks->prior_grad(a, 0, h->ntiles, st));
   CK(h->ks->fused(a, h->opt.loss, h->cal ? 1 : 0, h->TPV, h->fused_grid, h->NT, h->fused_smem, st));
   if (h->cal) {   // without calibration the fused kernel's last CTA finalises the groups
     CK(launch_bias_grad(a, h->ga, st));
@@ -675,6 +677,9 @@ int init_impl(prism_handle* h, const prism_volume* vols, int n_vols, const std::
   RC(h->alloc(&h->d_xf, 2 * static_cast<size_t>(h->XF) * Vp));
   RC(h->alloc(&h->d_hsp, static_cast<size_t>(h->K + 3) * Vp));
   RC(h->alloc(&h->d_lp, Vp));
+  const size_t pg_len = (h->nb && o.fused && h->TPV > 1) ? static_cast<size_t>(4 * h->K + 4) * Vp : 1;
+  RC(h->alloc(&h->d_pg, pg_len));
+  CK(cudaMemsetAsync(h->d_pg, 0, sizeof(float) * pg_len, st));
   RC(h->alloc(&h->d_gU, Vp));
   RC(h->alloc(&h->d_tile_ab, h->ab_len));
   RC(h->alloc(&h->d_tile_red, 4 * static_cast<size_t>(h->ntiles)));
@@ -860,9 +865,29 @@ int init_impl(prism_handle* h, const prism_volume* vols, int n_vols, const std::
 }
 
 int choose_shape(const prism_options& o, int64_t V, int* tpv, int* nt) {
-  // measured on GB300 (K = 3 and 5, MSE and NLL): one thread per voxel from 32,768 voxels;
-  // below, four lanes per voxel fill the SMs better (1.1-1.9x); sixteen only for the smallest
-  *tpv = o.threads_per_voxel ? o.threads_per_voxel : (V >= 32768 ? 1 : (V >= 2048 ? 4 : 16));
+  // Measured on GB300 (bundle phantoms, K = 3 and 5, MSE and NLL): sixteen lanes per voxel
+  // below 2,048 voxels, four below 32,768 (1.1-1.9x faster than one). Above, one thread per
+  // voxel, except where its 128-voxel tiles come to about one wave of the SMs' resident CTAs
+  // (0.75-1.25 waves: the last tiles then run nearly alone); four lanes then balance the SMs
+  // better (40^3: 7-19 % faster). Calibrated fits keep one thread per voxel there (their
+  // four-lane loop is not packed).
+  if (o.threads_per_voxel) {
+    *tpv = o.threads_per_voxel;
+  } else if (V < 2048) {
+    *tpv = 16;
+  } else if (V < 32768) {
+    *tpv = 4;
+  } else {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      sms = 152;
+    }
+    // CTAs per SM of the one-thread-per-voxel kernel (3 for five fibers, NLL or calibration)
+    const int occ = (o.K >= 5 || o.loss == PRISM_LOSS_NLL || o.calibration) ? 3 : 4;
+    const double waves = static_cast<double>(V) / 128.0 / (static_cast<double>(sms) * occ);
+    *tpv = (!o.calibration && waves > 0.75 && waves <= 1.25) ? 4 : 1;
+  }
   // the fused kernel is compiled for 128-thread CTAs (4 resident per SM)
   *nt = o.fused ? 128 : (o.cta_threads ? o.cta_threads : 128);
   return PRISM_OK;
@@ -1188,6 +1213,7 @@ extern "C" int prism_profile(prism_handle* h, int32_t n_iters, void* stream, flo
   for (int i = 0; i < n_iters && rc == PRISM_OK; ++i) {
     cudaError_t e = cudaEventRecord(ev[0], st);
     if (e == cudaSuccess && h->opt.lam_sp > 0.f) e = h->ks->prior_prep(a, 0, h->ntiles, st);
+    if (e == cudaSuccess && h->nb && h->TPV > 1) e = h->ks->prior_grad(a, 0, h->ntiles, st);
     if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
     if (e == cudaSuccess)
       e = h->ks->fused(a, h->opt.loss, h->cal ? 1 : 0, h->TPV, h->fused_grid, h->NT, h->fused_smem, st);

@@ -81,6 +81,7 @@ struct IterArgs {
   float* xf;               // [2][4K+3][Vpad] fractions and unit directions (ping-pong by step parity)
   float* hsp;              // [K+3][Vpad] rho'(u) / |N| of the Huber-Laplacian prior
   float* lp;               // [Vpad] Huber-Laplacian prior value per voxel
+  float* pg;               // [4K+4][Vpad] neighbour priors for the fused kernel (k_prior_grad)
   const int32_t* nbr;      // [n_nbr][Vpad] same-patch masked neighbour slots or -1
   const uint32_t* vcoord;  // [Vpad] x | y << 10 | z << 20
   const uint32_t* vflag;   // [Vpad] bits 0-5 TV neighbours (+x,-x,+y,-y,+z,-z) masked; bits 8-12 |N(x)|

@@ -123,6 +123,13 @@ cudaError_t l_prior_prep(const IterArgs& a, int tb, int te, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+cudaError_t l_prior_grad(const IterArgs& a, int tb, int te, cudaStream_t st) {
+  const int64_t n = static_cast<int64_t>(te - tb) * a.TV;
+  if (n <= 0) return cudaSuccess;
+  k_prior_grad<kK><<<nblocks(n, 128), 128, 0, st>>>(a, tb, te);
+  return cudaGetLastError();
+}
+
 cudaError_t l_prior(const IterArgs& a, const PlainArgs& p, cudaStream_t st) {
   const int g = p.tile_end - p.tile_begin;
   if (g <= 0) return cudaSuccess;
@@ -149,7 +156,7 @@ cudaError_t l_stitch(const IterArgs& a, const int32_t* sov, int64_t n_out, const
 #define PRISM_CAT2(a, b) a##b
 #define PRISM_CAT(a, b) PRISM_CAT2(a, b)
 const KernelSet& PRISM_CAT(kernels_k, PRISM_K)() {
-  static const KernelSet ks = {l_fused, l_fused_occupancy, l_transform, l_synth, l_adjoint, l_prior_prep, l_prior, l_fibers, l_stitch};
+  static const KernelSet ks = {l_fused, l_fused_occupancy, l_transform, l_synth, l_adjoint, l_prior_prep, l_prior_grad, l_prior, l_fibers, l_stitch};
   return ks;
 }
 

@@ -17,6 +17,7 @@ struct KernelSet {
   cudaError_t (*adjoint)(const IterArgs& a, const PlainArgs& p, int cal, int tpv, int nt, size_t smem,
                          cudaStream_t st);
   cudaError_t (*prior_prep)(const IterArgs& a, int tb, int te, cudaStream_t st);
+  cudaError_t (*prior_grad)(const IterArgs& a, int tb, int te, cudaStream_t st);
   cudaError_t (*prior)(const IterArgs& a, const PlainArgs& p, cudaStream_t st);
   cudaError_t (*fibers)(const IterArgs& a, const int32_t* slot_of_vox, int64_t V, float rel, float* dirs,
                         float* fracs, uint8_t* peaks, cudaStream_t st);
