@@ -9,6 +9,8 @@
 - HCP-shaped brain: 740,110 voxels, N = 288, MSE + neighbour priors, in the launch
   configuration bench.py times (fused, one thread per voxel, CUDA graph): two iterations,
   then the parameters of sampled whole patches against the oracle's two iterations.
+- DiSCo1-shaped fit: 40^3, N = 364, K = 5, Rician NLL with the topology and smoothness priors,
+  in its default launch configuration: one iteration, sampled whole patches.
 - mixed batch: 8 volumes with 96/288/360-measurement schemes, NLL + calibration, in full.
 """
 import types
@@ -172,6 +174,38 @@ def test_brain_bench_configuration_sampled_patches():
         _, _, g, _ = O.value_and_grad(ov, th, gp, n_norm=ov.n_mask)
         th = adam.step("theta", th, g)
     diff = np.abs(th2[ov.sel] - th.numpy())
+    assert float(diff.max()) < 3e-4, float(diff.max())
+
+
+def test_disco_shaped_configuration_sampled_patches():
+    """The DiSCo1-shaped fit of bench.py --workload disco (40^3, N = 364 up to b = 13,192, K = 5,
+    Rician NLL, topology and smoothness priors) in its default launch configuration (on a GB300
+    four lanes per voxel: 500 tiles of 128 voxels would fill 456 resident CTAs 1.1 times), one
+    graph-replayed iteration: the parameters of sampled whole patches against the oracle's Adam
+    step from the same start and group parameters."""
+    sch = P.make_scheme(4, [(1000, 90), (3000, 90), (7000, 90), (13192, 90)], 0)
+    vol = P.bundle_phantom(0, edge=40, snr=50.0, scheme=sch, device="cuda")
+    K = 5
+    kw = dict(K=K, loss="nll", patch_dim=16, lam_rep=0.01, lam_sparse=0.02, lam_sp=0.01, lam_dir=0.005,
+              lam_orphan=0.01, lam_order=0.01)
+    import paper_2604_00250_gb300 as prism
+    v = types.SimpleNamespace(mask=vol.mask, signal=torch.as_tensor(vol.signal).cuda(), bvals=vol.bvals,
+                              bvecs=vol.bvecs, init=None)
+    f = prism.Fitter([v], prism.options(fused=1, use_graph=1, **kw))
+    th0 = f.params_host()
+    gp = split_groups(f.groups().copy(), f)[0]
+    f.step(1)
+    f.sync()
+    th1 = f.params_host()
+    f.close()
+    ids, _ = _patch_ids(vol, 16, 4)
+    ov = O.OracleVolume(vol.mask, vol.signal, vol.bvals, vol.bvecs, oracle_opts(**kw), patches=ids)
+    th = torch.as_tensor(th0[ov.sel]).double()
+    adam = O.Adam(ov.opts)
+    adam.t += 1
+    _, _, g, _ = O.value_and_grad(ov, th, gp, n_norm=ov.n_mask)
+    ref = adam.step("theta", th, g).numpy()
+    diff = np.abs(th1[ov.sel] - ref)
     assert float(diff.max()) < 3e-4, float(diff.max())
 
 
