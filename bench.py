@@ -222,7 +222,7 @@ def run_ours(args):
     sig_dev = torch.as_tensor(vol.signal, device=dev)
     vdev = types.SimpleNamespace(mask=vol.mask, signal=sig_dev, bvals=vol.bvals, bvecs=vol.bvecs, init=None)
     opts = prism.options(K=K_FIB, loss="mse", patch_dim=16, fused=1, use_graph=1, autotune=int(args.autotune),
-                         **PRIORS)
+                         threads_per_voxel=args.threads_per_voxel, **PRIORS)
     f = prism.Fitter([vdev], opts)
     stream = torch.cuda.current_stream()
     # ---- timed region: K fused iterations (graph replay), inputs resident in HBM
@@ -250,7 +250,7 @@ def run_ours(args):
     nb0 = 2 * (int(np.count_nonzero(np.asarray(vol.bvals) == 0)) // 2)
     achieved = V * ((N - nb0) * FLOPS_PER_PAIR + nb0 * FLOPS_PER_B0_PAIR) / (fused_ms / 1e3) / 1e12
     loss_last = float(f.loss()[0])
-    tile = {"threads_per_voxel": None}
+    tile = f.shape()
     f.close()
     # ---- plain path: separate launches per patch and step, no graph
     unfused = None
@@ -318,14 +318,15 @@ def run_ours(args):
             torch.set_num_threads(nt)
         cpu["value_1core"] = rate1
         cpu["sample_1core"] = f"1 fullest 16^3 patch ({nvox1} voxels) x 5 iterations, {dt1:.1f} s"
-    # per iteration: neighbour-prior preparation + fused kernel (groups finalised inside it)
-    launches = (2 if PRIORS["lam_sp"] > 0 else 1)
+    # per iteration: neighbour-prior preparation (+ the neighbour-prior rows with several lanes
+    # per voxel) + fused kernel (groups finalised inside it)
+    launches = 1 + (1 if PRIORS["lam_sp"] > 0 else 0) + (1 if tile["threads_per_voxel"] > 1 else 0)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": cfg_dict(V, {"timing": "CUDA events, graph replay, max over ranks",
-                                       "brain_scale": args.brain_scale}),
+                                       "brain_scale": args.brain_scale, "launch": tile}),
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
                              "frac": achieved / PEAK_FP32_TFLOPS,
                              "traffic": (V * TRAFFIC_BYTES_PER_VOXEL_ITER if TRAFFIC_BYTES_PER_VOXEL_ITER else None),
@@ -505,6 +506,8 @@ def main():
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--brain-scale", type=float, default=1.0,
                     help="scale the brain grid (profiling of smaller cases; 1.0 = the benchmark workload)")
+    ap.add_argument("--threads-per-voxel", type=int, default=0, choices=[0, 1, 4, 16],
+                    help="force the fused kernel's lanes per voxel (0 = chosen from the voxel count)")
     ap.add_argument("--e2e-iters", type=int, default=500)
     ap.add_argument("--cpu-patches", type=int, default=4)
     ap.add_argument("--cpu-iters", type=int, default=20)

@@ -131,6 +131,15 @@ int prism_sync(prism_handle* h, void* stream);
 int prism_info(const prism_handle* h, int64_t* n_vox, int32_t* n_groups, int32_t* q,
                int64_t* n_group_params, int64_t* iterations);
 
+/*
+ * Launch shape the handle runs with: lanes per voxel (1, 4 or 16; chosen at init from the
+ * voxel count unless prism_options.threads_per_voxel forces one), voxels per tile, and CTAs of
+ * the persistent fused kernel (0 for a plain handle). Any output pointer may be NULL. The paper
+ * has no counterpart: the shape is this implementation's. Errors: PRISM_E_INVALID_ARG for a
+ * NULL handle.
+ */
+int prism_get_shape(const prism_handle* h, int32_t* threads_per_voxel, int32_t* tile_voxels, int32_t* fused_grid);
+
 /* Raw parameters [V][Q] in mask order, to/from host or device memory (per `mem`). */
 int prism_get_params(prism_handle* h, float* out, int32_t mem, void* stream);
 int prism_set_params(prism_handle* h, const float* in, int32_t mem, void* stream);

@@ -291,6 +291,12 @@ class Fitter:
                                             ctypes.c_void_p(gg.data_ptr()), _stream_ptr(stream)))
         return gth, gg
 
+    def shape(self):
+        """Launch shape: lanes per voxel, voxels per tile, CTAs of the fused kernel."""
+        tpv, tv, grid = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _lib.check(self._lib.prism_get_shape(self._h, ctypes.byref(tpv), ctypes.byref(tv), ctypes.byref(grid)))
+        return dict(threads_per_voxel=tpv.value, tile_voxels=tv.value, fused_grid=grid.value)
+
     def profile(self, n_iters=10, stream=None):
         """Average ms per iteration: fused kernel, prior preparation, group kernels, total."""
         ms = (ctypes.c_float * 4)()

@@ -18,7 +18,7 @@ EXPORTS = [
     "prism_set_groups", "prism_get_loss", "prism_forward", "prism_backward", "prism_state_size",
     "prism_get_state", "prism_set_state", "prism_fit", "prism_fit_destroy", "prism_last_error",
     "prism_profile", "prism_grad_noalloc", "prism_microbench", "prism_get_fibers",
-    "prism_fit_init_slabs", "prism_stitch_slabs",
+    "prism_fit_init_slabs", "prism_stitch_slabs", "prism_get_shape",
 ]
 
 
@@ -77,6 +77,7 @@ def load():
         "prism_step": (ctypes.c_int, [vp, i32, vp]),
         "prism_sync": (ctypes.c_int, [vp, vp]),
         "prism_info": (ctypes.c_int, [vp, P(i64), P(i32), P(i32), P(i64), P(i64)]),
+        "prism_get_shape": (ctypes.c_int, [vp, P(i32), P(i32), P(i32)]),
         "prism_get_params": (ctypes.c_int, [vp, vp, i32, vp]),
         "prism_set_params": (ctypes.c_int, [vp, vp, i32, vp]),
         "prism_group_layout": (ctypes.c_int, [vp, vp]),

@@ -1036,6 +1036,15 @@ extern "C" int prism_info(const prism_handle* h, int64_t* n_vox, int32_t* n_grou
   return PRISM_OK;
 }
 
+extern "C" int prism_get_shape(const prism_handle* h, int32_t* threads_per_voxel, int32_t* tile_voxels,
+                               int32_t* fused_grid) {
+  if (!h) return fail(PRISM_E_INVALID_ARG, "handle is NULL");
+  if (threads_per_voxel) *threads_per_voxel = h->TPV;
+  if (tile_voxels) *tile_voxels = h->TV;
+  if (fused_grid) *fused_grid = h->opt.fused ? h->fused_grid : 0;
+  return PRISM_OK;
+}
+
 extern "C" int prism_get_params(prism_handle* h, float* out, int32_t mem, void* stream) {
   if (!h || !out) return fail(PRISM_E_INVALID_ARG, "NULL argument");
   cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -157,6 +157,7 @@ def test_brain_bench_configuration_sampled_patches():
     v = types.SimpleNamespace(mask=vol.mask, signal=torch.as_tensor(vol.signal).cuda(), bvals=vol.bvals,
                               bvecs=vol.bvecs, init=None)
     f = prism.Fitter([v], prism.options(fused=1, use_graph=1, **kw))
+    assert f.shape()["threads_per_voxel"] == 1 and f.shape()["tile_voxels"] == 128
     th0 = f.params_host()
     f.step(2)
     f.sync()
@@ -192,6 +193,10 @@ def test_disco_shaped_configuration_sampled_patches():
     v = types.SimpleNamespace(mask=vol.mask, signal=torch.as_tensor(vol.signal).cuda(), bvals=vol.bvals,
                               bvecs=vol.bvecs, init=None)
     f = prism.Fitter([v], prism.options(fused=1, use_graph=1, **kw))
+    # the default shape: four lanes per voxel where 128-voxel tiles fill the resident CTAs
+    # (three per SM for five fibers) 0.75-1.25 times
+    waves = vol.n_vox / 128 / (torch.cuda.get_device_properties(0).multi_processor_count * 3)
+    assert f.shape()["threads_per_voxel"] == (4 if 0.75 < waves <= 1.25 else 1)
     th0 = f.params_host()
     gp = split_groups(f.groups().copy(), f)[0]
     f.step(1)
