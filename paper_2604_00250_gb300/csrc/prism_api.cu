@@ -869,8 +869,7 @@ int choose_shape(const prism_options& o, int64_t V, int* tpv, int* nt) {
   // below 2,048 voxels, four below 32,768 (1.1-1.9x faster than one). Above, one thread per
   // voxel, except where its 128-voxel tiles come to about one wave of the SMs' resident CTAs
   // (0.75-1.25 waves: the last tiles then run nearly alone); four lanes then balance the SMs
-  // better (40^3: 7-19 % faster). Calibrated fits keep one thread per voxel there (their
-  // four-lane loop is not packed).
+  // better (40^3: 7-19 % faster; calibrated, 14-19 %).
   if (o.threads_per_voxel) {
     *tpv = o.threads_per_voxel;
   } else if (V < 2048) {
@@ -886,7 +885,7 @@ int choose_shape(const prism_options& o, int64_t V, int* tpv, int* nt) {
     // CTAs per SM of the one-thread-per-voxel kernel (3 for five fibers, NLL or calibration)
     const int occ = (o.K >= 5 || o.loss == PRISM_LOSS_NLL || o.calibration) ? 3 : 4;
     const double waves = static_cast<double>(V) / 128.0 / (static_cast<double>(sms) * occ);
-    *tpv = (!o.calibration && waves > 0.75 && waves <= 1.25) ? 4 : 1;
+    *tpv = (waves > 0.75 && waves <= 1.25) ? 4 : 1;
   }
   // the fused kernel is compiled for 128-thread CTAs (4 resident per SM)
   *nt = o.fused ? 128 : (o.cta_threads ? o.cta_threads : 128);

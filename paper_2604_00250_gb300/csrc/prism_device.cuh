@@ -314,19 +314,21 @@ __device__ __forceinline__ float warp_sum_range(float x) {
   for (int o = FIRST; o <= LAST; o <<= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
   return x;
 }
-// Reduce-scatter over a warp: every lane holds G values v[0..G-1] (G = 2, 4 or 8); on return
-// each lane holds the warp-wide sum of v[m] for m = its bits (4 .. 5 - log2 G) read as a binary
-// number, i.e. m = lane >> (5 - log2 G). Halving exchanges (xor 16, 8, ...) move half of the
-// remaining values per stage, then an all-reduce over the low lane bits: log2 G + (5 - log2 G)
-// shuffles of G - 1 + (5 - log2 G) values in all, instead of 5 G for G separate all-reduces.
-template <int G>
+// Reduce-scatter over each run of W consecutive lanes (W = 32: the whole warp): every lane
+// holds G values v[0..G-1] (G = 2, 4 or 8, G <= W); on return each lane holds the run-wide sum
+// of v[m] for m = the top log2 G bits of its index in the run, i.e. m = (lane % W) >> (log2 W -
+// log2 G). Halving exchanges (xor W/2, W/4, ...) move half of the remaining values per stage,
+// then an all-reduce over the low lane bits: log2 W shuffles of G - 1 + (log2 W - log2 G) values
+// in all, instead of G log2 W for G separate all-reduces.
+template <int G, int W = 32>
 __device__ __forceinline__ float warp_scatter_sum(float (&v)[G]) {
   static_assert(G == 2 || G == 4 || G == 8, "G must be 2, 4 or 8");
+  static_assert((W == 8 || W == 16 || W == 32) && G <= W, "W must be 8, 16 or 32 and at least G");
   constexpr int LG = (G == 2) ? 1 : (G == 4) ? 2 : 3;
   const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int st = 0; st < LG; ++st) {
-    const int o = 16 >> st;
+    const int o = (W / 2) >> st;
     const int half = G >> (st + 1);
     const bool hi = (lane & o) != 0;
 #pragma unroll
@@ -338,7 +340,7 @@ __device__ __forceinline__ float warp_scatter_sum(float (&v)[G]) {
   }
   float x = v[0];
 #pragma unroll
-  for (int o = 16 >> LG; o >= 1; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  for (int o = (W / 2) >> LG; o >= 1; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
   return x;
 }
 

@@ -826,21 +826,21 @@ __device__ __forceinline__ void finalize_groups(const IterArgs& a, double (*s_su
   }
 }
 
-// Whether the fused kernel takes two measurements per step in f32x2 arithmetic. One thread
-// per voxel: all but the calibrated NLL with five fibers (its packed form spills even at 170
-// registers and measured 11 % slower). Four lanes per voxel: without calibration. Sixteen
-// lanes per voxel (one pair per lane and chunk): never, the scalar loop measured 0-20 % faster.
+// Whether the fused kernel takes two measurements per step in f32x2 arithmetic: with one or
+// four lanes per voxel, except the calibrated NLL with five fibers (its packed form spills even
+// at 170 registers and measured 11 % slower). Sixteen lanes per voxel (one pair per lane and
+// chunk): never, the scalar loop measured 0-20 % faster.
 template <int K, int TPV, int LOSS, bool CAL>
 __host__ __device__ constexpr bool fused_packed() {
-  return (TPV == 1) ? !(CAL && LOSS == kLossNLL && K >= 5) : (TPV == 4 && !CAL);
+  return (TPV == 1 || TPV == 4) && !(CAL && LOSS == kLossNLL && K >= 5);
 }
 
 // CTAs per SM the fused kernel is compiled for: 4 (128 registers per thread) where the voxel
-// state fits, 3 (170 registers) for five fibers, the packed NLL and the calibrated variants
-// with one thread per voxel, which spill at 128 and measured 7-54 % faster at 3.
+// state fits, 3 (170 registers) for five fibers and the packed NLL and calibrated variants,
+// which spill at 128 and measured 7-54 % faster at 3.
 template <int K, int TPV, int LOSS, bool CAL>
 constexpr int fused_min_blocks() {
-  return ((K >= 5) || (TPV == 1 && CAL) || (fused_packed<K, TPV, LOSS, CAL>() && LOSS == kLossNLL)) ? 3 : 4;
+  return ((K >= 5) || (fused_packed<K, TPV, LOSS, CAL>() && (CAL || LOSS == kLossNLL))) ? 3 : 4;
 }
 
 template <int K, int TPV, int LOSS, bool CAL>
@@ -1021,7 +1021,7 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<K, TPV, LOSS,
         // leading pairs of b = 0 measurements (the group's table starts with them); the NLL
         // still needs the Bessel terms there, so it takes them as ordinary pairs
         const int i0 = (LOSS == kLossMSE) ? max(0, min(kChunk / 2, gr.nb0p - j * (kChunk / 2))) : 0;
-        if constexpr (CAL) {
+        if constexpr (CAL && TPV == 1) {
           // two packed steps (four measurements) per reduce-scatter of the alpha / beta
           // partials; the accumulators hold the negated values, so the stores negate
           const float2 B2 = make_float2(B, B);
@@ -1046,6 +1046,36 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<K, TPV, LOSS,
             if ((lane & 7) == 0 && 2 * i + m < cnt) {
               s_ab[(warp * 2) * a.Nmax + j * kChunk + 2 * i + m] = -su;
               s_ab[(warp * 2 + 1) * a.Nmax + j * kChunk + 2 * i + m] = -sr;
+            }
+          }
+        } else if constexpr (CAL) {
+          // several lanes per voxel: lane js takes pairs js, js + TPV, ...; two packed steps
+          // (four measurements) per reduce-scatter over the VW lanes that share js (one per
+          // voxel of the warp); value q of a lane is half q & 1 of its step q >> 1
+          const float2 B2 = make_float2(B, B);
+          constexpr int LVW = (VW == 8) ? 3 : (VW == 16) ? 4 : 5;
+#pragma unroll 1
+          for (int i = 0; i < kChunk / 2 / TPV; i += 2) {
+            float uu[4], rv[4];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int pi = (i + h) * TPV + js;
+              float2 u = make_float2(0.f, 0.f), r = make_float2(0.f, 0.f);
+              if (act && 2 * pi < cnt)
+                step2<K, true, LOSS, true>(DP, tab2[pi], yc2[pi * VW], make_float2(1.f, (2 * pi + 1 < cnt) ? 1.f : 0.f),
+                                           AP, inv_s2, B2, &u, &r);
+              uu[2 * h] = u.x;
+              uu[2 * h + 1] = u.y;
+              rv[2 * h] = r.x;
+              rv[2 * h + 1] = r.y;
+            }
+            const float su = warp_scatter_sum<4, VW>(uu);
+            const float sr = warp_scatter_sum<4, VW>(rv);
+            const int q = lv >> (LVW - 2);
+            const int n = 2 * ((i + (q >> 1)) * TPV + js) + (q & 1);
+            if ((lv & ((VW >> 2) - 1)) == 0 && n < cnt) {
+              s_ab[(warp * 2) * a.Nmax + j * kChunk + n] = -su;
+              s_ab[(warp * 2 + 1) * a.Nmax + j * kChunk + n] = -sr;
             }
           }
         } else if (act && cnt == kChunk && i0 == 0) {
