@@ -537,7 +537,7 @@ def test_ordering_kink_has_zero_derivative():
     th = _frac_theta(1, 3, [0.0, 0.0, 0.0], dirs=[[[1, 0, 0], [0, 1, 0], [0, 0, 1]]]).requires_grad_(True)
     _, parts = O.objective(ov, th, O.group_init(ov))
     (g,) = torch.autograd.grad(parts["order"], th)
-    assert float(parts["order"]) == 0.0 and float(g.abs().max()) == 0.0
+    assert float(parts["order"].detach()) == 0.0 and float(g.abs().max()) == 0.0
 
 
 def test_crossing_scores_hand_cases():
