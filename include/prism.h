@@ -98,7 +98,10 @@ typedef struct prism_options {
   float rprop_step_min, rprop_step_max; /* Rprop step bounds, 1e-6 and 50 */
   int32_t fused;          /* 1: persistent fused iteration kernel; 0: plain unfused per-patch launches */
   int32_t use_graph;      /* 1: replay the fused iteration from a CUDA graph */
-  int32_t threads_per_voxel; /* 1, 4 or 16 (measurements split across lanes); 0 = automatic */
+  int32_t threads_per_voxel; /* 1, 4 or 16 (measurements split across lanes); 0 = automatic:
+                                16 below 2,048 voxels, 4 below 32,768, else 1 except where
+                                128-voxel tiles come to 0.75-1.25 waves of the fused kernel's
+                                resident CTAs (then 4); prism_get_shape reports the choice */
   int32_t cta_threads;    /* plain path: 128 or 256 threads per CTA; 0 = automatic (the fused kernel uses 128) */
   int32_t autotune;       /* 1: time the candidate tile shapes at init and keep the fastest */
   int32_t seed;           /* seed of the default initialisation (init == NULL) */
