@@ -15,6 +15,7 @@
 #include <memory>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "prism.h"
@@ -447,9 +448,32 @@ static std::vector<int32_t> tile_queue_order(const std::vector<Tile>& tiles, int
   return order;
 }
 
+// A vector whose elements start uninitialised: the plan's large index tables are written in
+// full by its parallel passes, so a serial fill first would only add a pass over them.
+template <typename T>
+struct NoFillAlloc : std::allocator<T> {
+  template <typename U>
+  struct rebind {
+    using other = NoFillAlloc<U>;
+  };
+  NoFillAlloc() = default;
+  template <typename U>
+  NoFillAlloc(const NoFillAlloc<U>&) noexcept {}
+  template <typename U>
+  void construct(U* p) noexcept {
+    ::new (static_cast<void*>(p)) U;
+  }
+  template <typename U, typename... A>
+  void construct(U* p, A&&... a) {
+    ::new (static_cast<void*>(p)) U(std::forward<A>(a)...);
+  }
+};
+template <typename T>
+using RawVec = std::vector<T, NoFillAlloc<T>>;
+
 struct Plan {
-  std::vector<int32_t> slot_of_vox, slot_of_grid;
-  std::vector<int64_t> row_off;
+  RawVec<int32_t> slot_of_vox, slot_of_grid;
+  RawVec<int64_t> row_off;
 };
 
 int build_plan(prism_handle* h, const prism_volume* vols, int n_vols, Plan& pl) {
@@ -462,16 +486,17 @@ int build_plan(prism_handle* h, const prism_volume* vols, int n_vols, Plan& pl) 
   h->yhat_off.assign(n_vols + 1, 0);
   // counts
   int64_t Vtot = 0, grid_tot = 0;
-  std::vector<std::vector<int32_t>> vidx(n_vols);
+  std::vector<RawVec<int32_t>> vidx(n_vols);
   for (int g = 0; g < n_vols; ++g) {
     const prism_volume& v = vols[g];
     const int64_t ng = static_cast<int64_t>(v.nx) * v.ny * v.nz;
-    vidx[g].assign(ng, -1);
-    // mask-order index of every masked grid position: chunk counts, then chunk offsets
+    vidx[g].resize(ng);
+    // mask-order index of every grid position (-1 outside the mask): chunk counts, then chunk
+    // offsets
     constexpr int64_t kChunkN = 1 << 18;
     const int64_t nch = (ng + kChunkN - 1) / kChunkN;
     std::vector<int32_t> cc(nch + 1, 0);
-    parallel_chunks(nch, 4, [&](int64_t b, int64_t e) {
+    parallel_chunks(nch, 1, [&](int64_t b, int64_t e) {
       for (int64_t k = b; k < e; ++k) {
         int32_t n = 0;
         for (int64_t i = k * kChunkN; i < std::min(ng, (k + 1) * kChunkN); ++i) n += v.mask[i] != 0;
@@ -479,11 +504,10 @@ int build_plan(prism_handle* h, const prism_volume* vols, int n_vols, Plan& pl) 
       }
     });
     for (int64_t k = 0; k < nch; ++k) cc[k + 1] += cc[k];
-    parallel_chunks(nch, 4, [&](int64_t b, int64_t e) {
+    parallel_chunks(nch, 1, [&](int64_t b, int64_t e) {
       for (int64_t k = b; k < e; ++k) {
         int32_t n = cc[k];
-        for (int64_t i = k * kChunkN; i < std::min(ng, (k + 1) * kChunkN); ++i)
-          if (v.mask[i]) vidx[g][i] = n++;
+        for (int64_t i = k * kChunkN; i < std::min(ng, (k + 1) * kChunkN); ++i) vidx[g][i] = v.mask[i] ? n++ : -1;
       }
     });
     const int32_t c = cc[nch];
@@ -495,9 +519,10 @@ int build_plan(prism_handle* h, const prism_volume* vols, int n_vols, Plan& pl) 
   }
   h->vox0[n_vols] = Vtot;
   h->V = Vtot;
-  pl.slot_of_vox.assign(Vtot, -1);
-  pl.row_off.assign(Vtot, 0);
-  pl.slot_of_grid.assign(grid_tot, -1);
+  // every entry of the three tables is written by pass 2 below
+  pl.slot_of_vox.resize(Vtot);
+  pl.row_off.resize(Vtot);
+  pl.slot_of_grid.resize(grid_tot);
   // tiles
   int64_t yoff = 0, aboff = 0, tab = 0, gp = 0, yh = 0;
   int Nmax = 0;
@@ -570,10 +595,10 @@ int build_plan(prism_handle* h, const prism_volume* vols, int n_vols, Plan& pl) 
       }
       h->patches.push_back({tb, static_cast<int>(h->tiles.size())});
     }
-    // pass 2 (parallel): the slots of each patch's voxels, in C order within the patch
+    // pass 2 (parallel): the slots of each patch's voxels, in C order within the patch; grid
+    // positions outside the mask (the patch boxes cover the grid) get slot -1
     parallel_chunks(npatch, 16, [&](int64_t b0, int64_t e0) {
       for (int64_t pi = b0; pi < e0; ++pi) {
-        if (ptile[pi] < 0) continue;
         int lo[3], hi[3];
         patch_box(pi, lo, hi);
         int slot = ptile[pi] * TV;
@@ -582,7 +607,10 @@ int build_plan(prism_handle* h, const prism_volume* vols, int n_vols, Plan& pl) 
             for (int z = lo[2]; z < hi[2]; ++z) {
               const int64_t gi = (static_cast<int64_t>(x) * v.ny + y) * v.nz + z;
               const int32_t vi = vidx[g][gi];
-              if (vi < 0) continue;
+              if (vi < 0) {
+                pl.slot_of_grid[gr.grid_off + gi] = -1;
+                continue;
+              }
               const int64_t vg = h->vox0[g] + vi;
               pl.slot_of_vox[vg] = slot;
               pl.slot_of_grid[gr.grid_off + gi] = slot;
@@ -609,8 +637,8 @@ int build_plan(prism_handle* h, const prism_volume* vols, int n_vols, Plan& pl) 
   return PRISM_OK;
 }
 
-template <typename T>
-int upload(T* dst, const std::vector<T>& src, cudaStream_t st) {
+template <typename T, typename A>
+int upload(T* dst, const std::vector<T, A>& src, cudaStream_t st) {
   if (src.empty()) return PRISM_OK;
   CK(cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, st));
   return PRISM_OK;
