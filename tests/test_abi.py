@@ -154,3 +154,19 @@ def test_readout_entry_points_reject_null_handles(prism):
     assert lib.prism_get_fibers(None, None, None, None, ctypes.c_float(0.15), 0, None) == 1
     assert lib.prism_stitch_slabs(None, None, None, None, None, 0, None) == 1
     assert lib.prism_get_shape(None, None, None, None) == 1
+
+
+def test_host_plan_runs_on_a_machine_without_a_gpu(prism):
+    """Without a GPU, prism_fit_init still builds the whole host plan (voxel counts, patches,
+    tiles, slot tables) for a batch of unlike volumes, and then reports the first failing CUDA
+    call as PRISM_E_CUDA instead of crashing."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: the handle would be created")
+    rng = np.random.default_rng(5)
+    vols = [_vol((rng.random(shape) < dens).astype(np.uint8)) for shape, dens in
+            (((37, 23, 41), 0.6), ((8, 8, 8), 1.0), ((1, 1, 1), 1.0), ((50, 3, 17), 0.3))]
+    for kw in (dict(patch_dim=16), dict(patch_dim=4, threads_per_voxel=4, calibration=1)):
+        with pytest.raises(prism.PrismError) as e:
+            prism.Fitter(vols, prism.options(**kw))
+        assert e.value.code == 3
