@@ -86,6 +86,21 @@ def test_single_stick_closed_form(K):
     assert abs(got[2] - 0.2794310) < 1e-6        # exp(-1.275), computed by hand
 
 
+def test_highest_shell_closed_forms():
+    """At the highest b of the DiSCo1 scheme (13,192 s/mm^2, Sec. 3 "Datasets") the stick and
+    the zeppelin still follow Eq. 5 in FP64 down to their smallest values: stick exp(-b D_par
+    cos^2) at 0 / 45 / 90 deg, zeppelin exp(-b (D_par cos^2 + D_perp sin^2)) at 45 and 90 deg."""
+    bv, gv = _line_scheme(13192.0, [0.0, 45.0, 90.0])
+    mask = np.ones((1, 1, 1), np.uint8)
+    ov = _vol(mask, np.ones((1, len(bv)), np.float32), bv, gv, K=1, lam_rep=0, lam_sparse=0)
+    stick, _ = O.predict(ov, _single_fiber_theta(1, 1, [1.0, 0.0, 0.0], 60.0), O.group_init(ov))
+    zep, _ = O.predict(ov, _single_fiber_theta(1, 1, [1.0, 0.0, 0.0], -60.0), O.group_init(ov))
+    # hand values: b D_par = 22.4264, b D_perp = 5.2768
+    np.testing.assert_allclose(stick[0].numpy()[1:], [1.8211186041263214e-10, 1.3494882749125023e-05, 1.0],
+                               rtol=1e-12)
+    np.testing.assert_allclose(zep[0].numpy()[2:], [9.645540179499184e-07, 0.005108752672315215], rtol=1e-12)
+
+
 def test_zeppelin_only_closed_form():
     """f_intra = 0: E = exp(-b (D_par cos^2 + D_perp sin^2)); at 90 deg exp(-b D_perp)."""
     bv, gv = _line_scheme(2000.0, [90.0, 0.0])
