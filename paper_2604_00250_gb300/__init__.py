@@ -103,7 +103,8 @@ def _volume_struct(vol, keep):
             ip = init.ctypes.data
     keep.extend([mask, bvals, bvecs, sig, init])
     nx, ny, nz = mask.shape
-    return _lib.Volume(nx, ny, nz, N, mem, 0, mask.ctypes.data, sp, bvals.ctypes.data, bvecs.ctypes.data, ip)
+    norm = int(getattr(vol, "norm_count", 0) or 0)
+    return _lib.Volume(nx, ny, nz, N, mem, norm, mask.ctypes.data, sp, bvals.ctypes.data, bvecs.ctypes.data, ip)
 
 
 def _volumes_array(volumes, keep):
@@ -135,6 +136,7 @@ class Fitter:
             arr, n = _volumes_array(volumes, keep)
             _lib.check(lib.prism_fit_init(arr, n, ctypes.byref(self.opts), _stream_ptr(stream), ctypes.byref(h)))
         self._h = h
+        self._fwd_token = None      # identifies the handle's last prism_forward (PrismLoss)
         V, G, Q, GP, it = (ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64(),
                            ctypes.c_int64())
         _lib.check(lib.prism_info(h, ctypes.byref(V), ctypes.byref(G), ctypes.byref(Q), ctypes.byref(GP),
@@ -171,10 +173,16 @@ class Fitter:
 
     # -- iterations ------------------------------------------------------------
     def step(self, n=1, stream=None):
+        self._fwd_token = None
         _lib.check(self._lib.prism_step(self._h, int(n), _stream_ptr(stream)))
 
     def sync(self, stream=None):
         _lib.check(self._lib.prism_sync(self._h, _stream_ptr(stream)))
+
+    def wait_probe(self, max_polls=1000, stream=None):
+        """Runs the library's check of its bounded device waits (prism_wait_probe): the next
+        sync() raises PrismError E_TIMEOUT, as every later one on this Fitter does."""
+        _lib.check(self._lib.prism_wait_probe(self._h, int(max_polls), _stream_ptr(stream)))
 
     @property
     def iterations(self):
@@ -200,6 +208,7 @@ class Fitter:
         t = torch.as_tensor(theta, dtype=torch.float32, device="cuda").contiguous()
         if tuple(t.shape) != (self.n_vox, self.Q):
             raise ValueError("theta must be [V, Q]")
+        self._fwd_token = None
         _lib.check(self._lib.prism_set_params(self._h, ctypes.c_void_p(t.data_ptr()), MEM_DEVICE,
                                               _stream_ptr(stream)))
         torch.cuda.current_stream().synchronize()
@@ -225,6 +234,14 @@ class Fitter:
                                               float(rel_thresh), MEM_HOST, _stream_ptr(None)))
         return d, f, p.astype(bool)
 
+    def groups_device(self, stream=None):
+        """Packed group parameters as a CUDA float32 tensor (a copy)."""
+        torch = _torch()
+        out = torch.empty(self.n_group_params, dtype=torch.float32, device="cuda")
+        _lib.check(self._lib.prism_get_groups(self._h, ctypes.c_void_p(out.data_ptr()), MEM_DEVICE,
+                                              _stream_ptr(stream)))
+        return out
+
     def group_layout(self):
         off = np.zeros(4 * self.n_groups + 1, dtype=np.int64)
         _lib.check(self._lib.prism_group_layout(self._h, off.ctypes.data))
@@ -237,6 +254,7 @@ class Fitter:
 
     def set_groups(self, packed):
         a = _host_f32(packed, (self.n_group_params,))
+        self._fwd_token = None
         _lib.check(self._lib.prism_set_groups(self._h, a.ctypes.data, MEM_HOST, _stream_ptr(None)))
 
     def group_view(self, packed=None):
@@ -264,23 +282,32 @@ class Fitter:
         return out[:n.value]
 
     def forward(self, theta=None, groups=None, want_yhat=False, stream=None):
-        """J per group (CUDA float64 [G]) and optionally y_hat (flat, volume-major rows)."""
+        """J per group (CUDA float64 [G]) and optionally y_hat (flat, volume-major rows).
+
+        A given `theta` ([V, Q] CUDA) or `groups` (packed, CUDA) becomes the handle's current
+        parameters, as with set_params / set_groups; None keeps the current ones."""
         torch = _torch()
         loss = torch.empty(self.n_groups, dtype=torch.float64, device="cuda")
         tp = gp = None
         if theta is not None:
             theta = theta.detach().to(torch.float32).contiguous()
+            if not theta.is_cuda or tuple(theta.shape) != (self.n_vox, self.Q):
+                raise ValueError(f"theta must be a CUDA tensor [V={self.n_vox}, Q={self.Q}]")
             tp = ctypes.c_void_p(theta.data_ptr())
         if groups is not None:
             groups = groups.detach().to(torch.float32).contiguous()
+            if not groups.is_cuda or tuple(groups.shape) != (self.n_group_params,):
+                raise ValueError(f"groups must be a CUDA tensor [{self.n_group_params}]")
             gp = ctypes.c_void_p(groups.data_ptr())
         yhat = None
         yp = None
         if want_yhat:
             yhat = torch.empty(self.yhat_len, dtype=torch.float32, device="cuda")
             yp = ctypes.c_void_p(yhat.data_ptr())
+        self._fwd_token = None
         _lib.check(self._lib.prism_forward(self._h, tp, gp, yp, ctypes.c_void_p(loss.data_ptr()),
                                            _stream_ptr(stream)))
+        self._fwd_token = object()
         return loss, yhat
 
     def backward(self, stream=None):
@@ -300,6 +327,7 @@ class Fitter:
     def profile(self, n_iters=10, stream=None):
         """Average ms per iteration: fused kernel, prior preparation, group kernels, total."""
         ms = (ctypes.c_float * 4)()
+        self._fwd_token = None
         _lib.check(self._lib.prism_profile(self._h, int(n_iters), _stream_ptr(stream), ms))
         return dict(fused_ms=ms[0], prep_ms=ms[1], group_ms=ms[2], iter_ms=ms[3])
 
@@ -313,6 +341,7 @@ class Fitter:
 
     def load_state(self, blob):
         buf = ctypes.create_string_buffer(blob, len(blob))
+        self._fwd_token = None
         _lib.check(self._lib.prism_set_state(self._h, buf, len(blob), _stream_ptr(None)))
 
 
@@ -342,20 +371,39 @@ def _make_autograd():
     torch = _torch()
 
     class PrismLoss(torch.autograd.Function):
-        """J(theta, groups) = sum_g J_g; forward = synthesis + data term + priors,
-        backward = hand-written adjoint (compartment exponentials recomputed)."""
+        """J(theta, groups) = sum_g J_g as a differentiable function of the raw voxel parameters
+        theta ([V, Q] CUDA) and the packed group parameters (CUDA, or None for the handle's
+        current ones, which then get no gradient). Forward: prism_forward (synthesis,
+        calibration, data term, priors). Backward: prism_backward, the hand-written adjoint,
+        which recomputes the compartment exponentials instead of storing them (Sec. 2.1: every
+        component is differentiable, so tissue and calibration parameters can be updated
+        jointly). Each node keeps its own evaluation point; when the handle has evaluated
+        another point since (a second node on the same Fitter, a step), backward first repeats
+        the forward at this node's point. The handle's current parameters are those of the
+        last evaluation."""
 
         @staticmethod
         def forward(ctx, theta, groups, fitter):
-            loss, _ = fitter.forward(theta, groups)
+            th = theta.detach().to(torch.float32).contiguous()
+            gp = groups.detach().to(torch.float32).contiguous() if groups is not None else fitter.groups_device()
+            loss, _ = fitter.forward(th, gp)
             ctx.fitter = fitter
+            ctx.token = fitter._fwd_token
+            ctx.point = (th, gp)
+            ctx.dtypes = (theta.dtype, groups.dtype if groups is not None else None)
             return loss.sum()
 
         @staticmethod
         def backward(ctx, gout):
-            gth, gg = ctx.fitter.backward()
+            f = ctx.fitter
+            if f._fwd_token is None or f._fwd_token is not ctx.token:
+                f.forward(*ctx.point)
+                ctx.token = f._fwd_token
+            gth, gg = f.backward()
             s = gout.to(torch.float32)
-            return gth * s, gg * s, None
+            g_theta = (gth * s).to(ctx.dtypes[0]) if ctx.needs_input_grad[0] else None
+            g_groups = (gg * s).to(ctx.dtypes[1]) if ctx.needs_input_grad[1] else None
+            return g_theta, g_groups, None
 
     return PrismLoss
 
