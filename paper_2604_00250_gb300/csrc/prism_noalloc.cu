@@ -8,10 +8,12 @@
 // pass every input and output buffer; the only other memory used is the fixed
 // file-scope array below, which every GPU that loads the library holds until exit.
 //
-// It evaluates, for n_vox voxels of one group, the MSE data term (Eq. 8) with the
-// repulsion and sparsity priors (no calibration, no neighbour priors), on raw signal
-// rows b0-normalised inline, exactly as prism_forward / prism_backward do for such a
-// problem, and writes J and dJ/dtheta. The paper has no counterpart of this entry point.
+// It evaluates, for n_vox voxels of one group, the mean squared error of the predicted
+// signal (summed over measurements, divided by n_vox) plus the mean direction-repulsion and
+// minor-fraction sparsity penalties (no calibration, no neighbour priors), on raw signal rows
+// that it divides by each voxel's mean b <= 50 signal, exactly as prism_forward /
+// prism_backward do for such a problem, and writes J and dJ/dtheta. The paper has no
+// counterpart of this entry point.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -66,8 +68,12 @@ __global__ void __launch_bounds__(kNaThreads) k_grad_noalloc(const float* __rest
   transform<K>(th, P);
   float ffin[K], fomf[K];
   fiber_weights<K>(P, ffin, fomf);
-  // b0 normalisation (Sec. 2.5): mean of the b <= 50 measurements, table rows flagged by pad0
+  // b0 normalisation: mean of the b <= 50 measurements, table rows flagged by pad0. A mean
+  // that is not positive and finite is replaced by 1 for this voxel's arithmetic (as the
+  // handle path's b0 statistics do) and marks the voxel: its gradient row and the loss
+  // become NaN, since an asynchronous call cannot return an error code for it.
   float b0 = 1.f;
+  bool bad = false;
   if (act) {
     double m = 0.0;
     int nb0 = 0;
@@ -76,7 +82,12 @@ __global__ void __launch_bounds__(kNaThreads) k_grad_noalloc(const float* __rest
         m += signal[v * N + n];
         ++nb0;
       }
-    b0 = static_cast<float>(m / nb0);
+    const double mean = m / nb0;
+    if (mean > 0.0 && mean < 1e300) {
+      b0 = static_cast<float>(mean);
+    } else {
+      bad = true;
+    }
   }
   Acc<K> A;
   acc_zero<K>(A);
@@ -96,13 +107,14 @@ __global__ void __launch_bounds__(kNaThreads) k_grad_noalloc(const float* __rest
   const float ploss = act ? priors<K>(pa, P, 0, inv_M, nullptr, gS0, gf, gd) : 0.f;
   float g[Q];
   chain_raw<K>(P, gS0, gf, gd, gfin, g);
+  const float qnan = __int_as_float(0x7fc00000);
   if (act) {
 #pragma unroll
-    for (int q = 0; q < Q; ++q) grad[v * Q + q] = g[q];
+    for (int q = 0; q < Q; ++q) grad[v * Q + q] = bad ? qnan : g[q];
   }
   double out[3];
-  block_reduce3(act ? static_cast<double>(A.l1 * inv_M) : 0.0, act ? static_cast<double>(ploss) : 0.0, 0.0,
-                s_red, out);
+  const double dl = bad ? static_cast<double>(qnan) : static_cast<double>(A.l1 * inv_M);
+  block_reduce3(act ? dl : 0.0, act ? static_cast<double>(ploss) : 0.0, 0.0, s_red, out);
   if (threadIdx.x == 0) {
     partial[blockIdx.x] = out[0] + out[1];
     __threadfence();
@@ -147,6 +159,14 @@ extern "C" int prism_grad_noalloc(const float* signal, const float* bvals, const
   for (int n = 0; n < n_meas; ++n) {
     const double b = bvals[n];
     if (!std::isfinite(b) || b < 0.0) return prism_record_error(PRISM_E_INVALID_ARG, "prism_grad_noalloc: bad b-value");
+    // the b-vector rules of prism_fit_init: finite, and unit length where b > 50
+    const float gx = bvecs[3 * n], gy = bvecs[3 * n + 1], gz = bvecs[3 * n + 2];
+    if (!std::isfinite(gx) || !std::isfinite(gy) || !std::isfinite(gz))
+      return prism_record_error(PRISM_E_INVALID_ARG, "prism_grad_noalloc: non-finite b-vector");
+    if (b > 50.0 && std::fabs(std::sqrt(gx * gx + gy * gy + gz * gz) - 1.f) > 1e-3f)
+      return prism_record_error(PRISM_E_INVALID_ARG,
+                                ("prism_grad_noalloc: b-vector " + std::to_string(n) +
+                                 " of a b > 50 measurement is not unit length").c_str());
     MeasRow r;
     r.gx = bvecs[3 * n];
     r.gy = bvecs[3 * n + 1];
