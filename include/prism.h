@@ -66,7 +66,13 @@ typedef struct prism_volume {
   int32_t nx, ny, nz;     /* grid size, each >= 1 */
   int32_t n_meas;         /* N >= 1; at least one b <= 50 s/mm^2 (used for b0 normalisation) */
   int32_t mem;            /* PRISM_MEM_HOST or PRISM_MEM_DEVICE: where `signal` and `init` live */
-  int32_t reserved;
+  int32_t norm_count;     /* |M| that divides the MSE and the prior means (Eq. 8, Sec. 2.4): 0 = the
+                             masked voxels of this mask. A caller that fits some whole patches of
+                             a larger volume (a shard of it on one GPU) passes that volume's mask
+                             restricted to those patches and the whole volume's masked count here;
+                             without calibration and with the MSE, every voxel then follows the
+                             whole-volume fit exactly (patches are independent problems).
+                             E_SHAPE if 0 < norm_count < the masked voxels of this mask. */
   const uint8_t* mask;    /* HOST [nx][ny][nz], C order, nonzero = inside the brain mask */
   const float* signal;    /* [V_vol][N] raw magnitudes of the masked voxels in mask order */
   const float* bvals;     /* HOST [N] b-values, s/mm^2 (>= 0) */
@@ -129,6 +135,18 @@ int prism_step(prism_handle* h, int32_t n_iters, void* stream);
 
 /* Synchronises `stream` and reports any device-side status (E_TIMEOUT, E_NONFINITE) or CUDA error. */
 int prism_sync(prism_handle* h, void* stream);
+
+/*
+ * Check of the bounded device-side waits (the paper has no counterpart; for tests of the
+ * error path). Enqueues one small kernel that waits, with the same bounded wait the fused
+ * kernel uses for its bulk copies, on a barrier phase that nothing completes: no copy is
+ * issued and nothing arrives, so nothing is left in flight. After max_polls polls
+ * (1 .. 1,048,576) the wait gives up, the kernel sets the handle's timeout status and
+ * returns; the next prism_sync returns PRISM_E_TIMEOUT, as every later one on this handle
+ * does. The CUDA context and other handles stay usable. E_INVALID_ARG for a NULL handle or
+ * max_polls out of range.
+ */
+int prism_wait_probe(prism_handle* h, int32_t max_polls, void* stream);
 
 /* Sizes: total voxels V, groups, Q, total packed group-parameter floats, iterations done. */
 int prism_info(const prism_handle* h, int64_t* n_vox, int32_t* n_groups, int32_t* q,
@@ -206,7 +224,8 @@ int prism_get_loss(prism_handle* h, double* loss, double* hist, int32_t max_iter
 /*
  * Forward evaluation at `theta` (DEVICE [V][Q], or NULL = current parameters)
  * and `groups` (DEVICE packed, or NULL = current): synthesis, calibration and
- * data term, plus the prior values. Writes y_hat (DEVICE, NULL to skip; group g
+ * data term, plus the prior values. A given theta / groups becomes the handle's
+ * current parameters (as by prism_set_params / prism_set_groups). Writes y_hat (DEVICE, NULL to skip; group g
  * at offset sum_{g'<g} V_g' N_g', rows [V_g][N_g] in mask order) and J_g
  * (DEVICE double [G]). Keeps the residual derivative dL/dy_hat (V x N, not the
  * V x N x K compartment terms) for prism_backward.
@@ -268,16 +287,22 @@ int prism_fit(const prism_volume* vols, int32_t n_vols, const prism_options* opt
  * routine: beyond the caller's buffers it uses one fixed 128 KiB array inside the
  * library, which every GPU that loads the library keeps until the process exits.
  *
- * Evaluates, for n_vox voxels forming one group, J = MSE data term (Eq. 8, divided by
- * n_vox) + lam_rep * mean repulsion + lam_sparse * mean sparsity (Sec. 2.4), without
- * calibration or neighbour priors, on raw signal rows that it b0-normalises itself
- * (mean of the b <= 50 measurements), and its gradient -- the same values prism_forward
- * and prism_backward give for that problem.
+ * Evaluates, for n_vox voxels forming one group, J = (sum of squared differences between
+ * predicted and measured signal over all voxels and measurements) / n_vox + lam_rep * mean
+ * fiber-direction repulsion + lam_sparse * mean minor-fraction sparsity, without
+ * calibration or neighbour priors, on raw signal rows that it divides by each voxel's mean
+ * b <= 50 signal itself, and its gradient -- the same values prism_forward and
+ * prism_backward give for that problem.
  *   signal  DEVICE [n_vox][n_meas] raw magnitudes;  theta DEVICE [n_vox][4K+5] raw parameters
  *   bvals   HOST [n_meas];  bvecs HOST [n_meas][3]
  *   grad    DEVICE [n_vox][4K+5] (written);  loss DEVICE double[1] (written)
  * Limits: 1 <= n_vox <= 1,048,576, 1 <= n_meas <= 1024, 1 <= K <= 5 (E_SHAPE /
- * E_INVALID_ARG otherwise, before any device work); at least one b <= 50 measurement.
+ * E_INVALID_ARG otherwise, before any device work); at least one b <= 50 measurement;
+ * b-values finite and >= 0, b-vectors finite and of unit length where b > 50, as for
+ * prism_fit_init (E_INVALID_ARG). The signal is read on the GPU after the call returns, so
+ * a voxel whose mean b <= 50 signal is not positive and finite (which prism_fit_init
+ * refuses with E_NONFINITE) is reported in the outputs instead: its gradient row and the
+ * loss are NaN; the other rows are computed as usual.
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture begins.
  * Every call shares the array and leaves its contents behind (it clears what must start

@@ -2,7 +2,7 @@
 
 Fiber directions are used directly as peaks (Sec. 3 "Configuration"); a fiber
 counts as a peak when its share of the white-matter fraction is at least
-`rel_thresh` (reading R20). Angles are arccos|d . d'| in degrees (directions
+`rel_thresh` (reading R20: the paper gives no threshold; 0.15 by default). Angles are arccos|d . d'| in degrees (directions
 are sign-free). Best-match angular error matches each reference fiber to its
 closest predicted fiber (Sec. 3 "Tracking & metrics").
 """
@@ -78,7 +78,9 @@ def best_match_error(theta, gt_dirs, gt_ffib, K, rel_thresh=0.15, match_deg=20.0
 
 
 def crossing_scores(dirs, peaks, gt_dirs, gt_ffib, case, match_deg=20.0):
-    """Crossing-benchmark scores (Sec. 3 "Tracking & metrics"; reading R31).
+    """Crossing-benchmark scores (Sec. 3 "Tracking & metrics"; reading R31: best-match error
+    per ground-truth fiber; detection pairs peaks and fibers one to one, greedily by angle,
+    within `match_deg`).
 
     dirs [V, K, 3] fitted unit directions, peaks [V, K] bool (R20), gt_dirs [V, F, 3],
     gt_ffib [V, F] (a ground-truth fiber exists where > 0), case [V] integer label.

@@ -18,7 +18,7 @@ EXPORTS = [
     "prism_set_groups", "prism_get_loss", "prism_forward", "prism_backward", "prism_state_size",
     "prism_get_state", "prism_set_state", "prism_fit", "prism_fit_destroy", "prism_last_error",
     "prism_profile", "prism_grad_noalloc", "prism_microbench", "prism_get_fibers",
-    "prism_fit_init_slabs", "prism_stitch_slabs", "prism_get_shape",
+    "prism_fit_init_slabs", "prism_stitch_slabs", "prism_get_shape", "prism_wait_probe",
 ]
 
 
@@ -31,7 +31,7 @@ class PrismError(RuntimeError):
 class Volume(ctypes.Structure):
     _fields_ = [
         ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
-        ("n_meas", ctypes.c_int32), ("mem", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("n_meas", ctypes.c_int32), ("mem", ctypes.c_int32), ("norm_count", ctypes.c_int32),
         ("mask", ctypes.c_void_p), ("signal", ctypes.c_void_p), ("bvals", ctypes.c_void_p),
         ("bvecs", ctypes.c_void_p), ("init", ctypes.c_void_p),
     ]
@@ -76,6 +76,7 @@ def load():
         "prism_fit_init": (ctypes.c_int, [P(Volume), i32, P(Options), vp, P(vp)]),
         "prism_step": (ctypes.c_int, [vp, i32, vp]),
         "prism_sync": (ctypes.c_int, [vp, vp]),
+        "prism_wait_probe": (ctypes.c_int, [vp, i32, vp]),
         "prism_info": (ctypes.c_int, [vp, P(i64), P(i32), P(i32), P(i64), P(i64)]),
         "prism_get_shape": (ctypes.c_int, [vp, P(i32), P(i32), P(i32)]),
         "prism_get_params": (ctypes.c_int, [vp, vp, i32, vp]),

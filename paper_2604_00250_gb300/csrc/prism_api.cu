@@ -512,6 +512,9 @@ int build_plan(prism_handle* h, const prism_volume* vols, int n_vols, Plan& pl) 
     });
     const int32_t c = cc[nch];
     if (c == 0) return fail(PRISM_E_SHAPE, "volume " + std::to_string(g) + ": empty mask");
+    if (v.norm_count != 0 && v.norm_count < c)
+      return fail(PRISM_E_SHAPE, "volume " + std::to_string(g) + ": norm_count " + std::to_string(v.norm_count) +
+                                     " is below the " + std::to_string(c) + " masked voxels");
     h->vox0[g] = Vtot;
     Vtot += c;
     h->groups[g].grid_off = grid_tot;
@@ -535,7 +538,7 @@ int build_plan(prism_handle* h, const prism_volume* vols, int n_vols, Plan& pl) 
     gr.N = v.n_meas;
     gr.N4 = (v.n_meas + 3) / 4 * 4;
     gr.n_vox = static_cast<int32_t>(h->vox0[g + 1] - h->vox0[g]);
-    gr.inv_M = 1.f / static_cast<float>(gr.n_vox);
+    gr.inv_M = 1.f / static_cast<float>(v.norm_count > 0 ? v.norm_count : gr.n_vox);
     gr.calib = h->cal ? 1 : 0;
     gr.table_off = static_cast<int32_t>(tab);
     gr.nb0p = meas_order(v, h->cal, h->order);
@@ -854,7 +857,7 @@ int init_impl(prism_handle* h, const prism_volume* vols, int n_vols, const std::
       }
       CK(launch_scatter_params(in, h->d_slot_of_vox + h->vox0[g], Vg, Q, Vp, h->d_theta, st));
     } else {
-      CK(launch_default_init(h->d_slot_of_vox + h->vox0[g], Vg, h->K, Vp,
+      CK(launch_default_init(h->d_slot_of_vox + h->vox0[g], h->d_vcoord, v.ny, v.nz, Vg, h->K, Vp,
                              static_cast<uint64_t>(o.seed) * 1315423911ull + g, h->d_theta, st));
     }
     // free per-volume temporaries (after the work that reads them)
@@ -1049,6 +1052,13 @@ extern "C" int prism_sync(prism_handle* h, void* stream) {
   CK(cudaMemcpy(&status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
   if (status & kStTimeout) return fail(PRISM_E_TIMEOUT, "a bounded device wait (table bulk copy) timed out");
   if (status & kStNonfinite) return fail(PRISM_E_NONFINITE, "the objective became non-finite");
+  return PRISM_OK;
+}
+
+extern "C" int prism_wait_probe(prism_handle* h, int32_t max_polls, void* stream) {
+  if (!h) return fail(PRISM_E_INVALID_ARG, "handle is NULL");
+  if (max_polls < 1 || max_polls > (1 << 20)) return fail(PRISM_E_INVALID_ARG, "max_polls must be in 1..1048576");
+  CK(launch_wait_probe(h->d_status, max_polls, static_cast<cudaStream_t>(stream)));
   return PRISM_OK;
 }
 

@@ -46,7 +46,8 @@ __global__ void k_b0_stats(const float* __restrict__ sig, int64_t V, int N, cons
   if (threadIdx.x == 0) part[blockIdx.x] = s[0];
 }
 
-// sigma init (reading R18): pooled std of the normalised b0 repeats, clamped >= 1e-3.
+// sigma init (Sec. 2.3 learns sigma but does not say where it starts): pooled std of the
+// normalised b0 repeats, clamped >= 1e-3.
 __global__ void k_sigma_init(const double* part, int nblocks, int64_t V, int nb0, float fallback,
                              float* sigma_log) {
   if (threadIdx.x != 0) return;
@@ -210,12 +211,17 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
 }
 __device__ __forceinline__ double u01(uint64_t h) { return ((h >> 11) + 0.5) * (1.0 / 9007199254740992.0); }
 
-// Default start: S0 = 1, equal fractions, f_intra = 0.5, directions uniform on the sphere.
-__global__ void k_default_init(const int32_t* __restrict__ slot_of_vox, int64_t V, int K, int Vpad,
-                               uint64_t seed, float* __restrict__ theta) {
-  const int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (v >= V) return;
-  const int slot = slot_of_vox[v];
+// Default start: S0 = 1, equal fractions, f_intra = 0.5, directions uniform on the sphere,
+// drawn per grid position (so that a voxel starts from the same values whichever of the
+// volume's voxels share the handle).
+__global__ void k_default_init(const int32_t* __restrict__ slot_of_vox, const uint32_t* __restrict__ vcoord, int ny,
+                               int nz, int64_t V, int K, int Vpad, uint64_t seed, float* __restrict__ theta) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= V) return;
+  const int slot = slot_of_vox[i];
+  int cx, cy, cz;
+  unpack_coord(vcoord[slot], cx, cy, cz);
+  const int64_t v = (static_cast<int64_t>(cx) * ny + cy) * nz + cz;
   theta[slot] = static_cast<float>(log(exp(1.0) - 1.0));
   for (int i = 0; i < K + 3; ++i) theta[static_cast<size_t>(1 + i) * Vpad + slot] = 0.f;
   for (int k = 0; k < K; ++k) {
@@ -424,7 +430,8 @@ __global__ void __launch_bounds__(kNGrid) k_bias_grad_x(const IterArgs a, const 
   g.gred[gr.gp_off + 4 + 2 * gr.N4 + c] = acc;
 }
 
-// Group finalisation (one block): objective with calibration regularisers (reading R11),
+// Group finalisation (one block): objective with the calibration regularisers of Sec. 2.4
+// (L2 on alpha, beta, b_lr and TV on B; the paper gives no weights: 1e-3 each by default),
 // loss history, Adam on sigma_log / alpha / beta / b_lr, table refresh, step counter.
 // mode bit 0: loss; bit 1: Adam + step; bit 2: export gradients.
 __global__ void __launch_bounds__(256) k_group_adam(const IterArgs a, const GroupArgs g, int mode) {
@@ -565,6 +572,23 @@ __global__ void k_table_refresh(const GroupArgs g, const IterArgs a) {
 // ---------------------------------------------------------------------------
 static inline int nblk(int64_t n, int b) { return static_cast<int>((n + b - 1) / b); }
 
+// The bounded-wait error path, exercised without a fault: one thread waits, with the bounded
+// wait the fused kernel uses for its bulk copies, on the first phase of a fresh mbarrier that
+// nothing completes (no copy is issued and nothing arrives). When the wait gives up after
+// `polls` polls, the timeout bit of the status word is set and the kernel returns.
+__global__ void k_wait_probe(int32_t* status, int polls) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  fence_mbar_init();
+  if (!mbar_wait(&bar, 0u, polls)) atomicOr(status, kStTimeout);
+}
+
+cudaError_t launch_wait_probe(int32_t* status, int polls, cudaStream_t st) {
+  k_wait_probe<<<1, 32, 0, st>>>(status, polls);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_group_reduce(const IterArgs& a, const GroupArgs& g, int what, cudaStream_t st) {
   dim3 grid((g.max_e + 255) / 256, g.max_split, g.G);
   k_group_reduce<<<grid, 256, 0, st>>>(a, g, what);
@@ -653,10 +677,10 @@ cudaError_t launch_gather_params(const float* th, const int32_t* sov, int64_t V,
   k_gather_params<<<nblk(V * Q, 256), 256, 0, st>>>(th, sov, V, Q, Vpad, out);
   return cudaGetLastError();
 }
-cudaError_t launch_default_init(const int32_t* sov, int64_t V, int K, int Vpad, uint64_t seed, float* th,
-                                cudaStream_t st) {
+cudaError_t launch_default_init(const int32_t* sov, const uint32_t* vcoord, int ny, int nz, int64_t V, int K,
+                                int Vpad, uint64_t seed, float* th, cudaStream_t st) {
   if (V == 0) return cudaSuccess;
-  k_default_init<<<nblk(V, 128), 128, 0, st>>>(sov, V, K, Vpad, seed, th);
+  k_default_init<<<nblk(V, 128), 128, 0, st>>>(sov, vcoord, ny, nz, V, K, Vpad, seed, th);
   return cudaGetLastError();
 }
 cudaError_t launch_gather_yhat(const float* ypack, const IterArgs& a, const int32_t* vos, const int64_t* roff,

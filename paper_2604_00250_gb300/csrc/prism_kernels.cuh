@@ -272,7 +272,8 @@ __device__ __forceinline__ float priors(const IterArgs& a, const Vox<K>& P, int 
   return val;
 }
 
-// Total-variation term of the upsampled bias field at voxel (x, y, z) (reading R11):
+// Total-variation term of the upsampled bias field at voxel (x, y, z) (Sec. 2.4 "Calibration
+// regularizers"; its form is not given there: sqrt((B(x+e) - B(x))^2 + eps) per axis):
 // forward pairs inside the mask count once; returns the value and adds dTV/dU(x) to gU.
 __device__ __forceinline__ float tv_term(const float* blr, int x, int y, int z, const GroupDev& gr,
                                          uint32_t fl, float B0, float w, float eps, float& gU) {
@@ -1336,12 +1337,13 @@ __global__ void k_fibers(const IterArgs a, const int32_t* __restrict__ slot_of_v
 }
 
 // Slab stitching (Sec. 3 "Configuration": overlapping slabs stitched by weighted averaging;
-// reading R29). Output voxel v takes the estimate at handle voxel src0[v] and, where two slabs
-// overlap, blends in the one at src1[v] with weight w1[v] (src0's weight is 1 - w1). The
-// later slab's fibers are matched to the earlier slab's by the permutation maximising
-// sum_k |d0_k . d1_pi(k)| (FP64 dot products, first maximum in lexicographic order), each
-// matched direction is flipped into the same hemisphere, then S0, fractions, f_intra and the
-// directions are averaged and the directions renormalised.
+// the ramp weights and the fiber matching are this library's choice). Output voxel v takes
+// the estimate at handle voxel src0[v] and, where two slabs overlap, blends in the one at
+// src1[v] with weight w1[v] (src0's weight is 1 - w1). The later slab's fibers are matched to
+// the earlier slab's by the permutation maximising sum_k |d0_k . d1_pi(k)| (FP64 dot
+// products, first maximum in lexicographic order), each matched direction is flipped into
+// the same hemisphere, then S0, fractions, f_intra and the directions are averaged and the
+// directions renormalised.
 template <int K>
 __global__ void k_stitch(const IterArgs a, const int32_t* __restrict__ slot_of_vox, int64_t n_out,
                          const int64_t* __restrict__ src0, const int64_t* __restrict__ src1,

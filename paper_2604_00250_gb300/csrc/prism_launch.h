@@ -79,11 +79,12 @@ cudaError_t launch_scatter_params(const float* in, const int32_t* slot_of_vox, i
                                   float* theta, cudaStream_t st);
 cudaError_t launch_gather_params(const float* theta, const int32_t* slot_of_vox, int64_t V, int Q, int Vpad,
                                  float* out, cudaStream_t st);
-cudaError_t launch_default_init(const int32_t* slot_of_vox, int64_t V, int K, int Vpad, uint64_t seed,
-                                float* theta, cudaStream_t st);
+cudaError_t launch_default_init(const int32_t* slot_of_vox, const uint32_t* vcoord, int ny, int nz, int64_t V, int K,
+                                int Vpad, uint64_t seed, float* theta, cudaStream_t st);
 cudaError_t launch_gather_yhat(const float* ypack, const IterArgs& a, const int32_t* vox_of_slot,
                                const int64_t* yhat_row_off, const int32_t* order, float* out, cudaStream_t st);
 cudaError_t launch_table_refresh(const GroupArgs& g, const IterArgs& a, cudaStream_t st);
 cudaError_t launch_adam_constants(const IterArgs& a, cudaStream_t st);
+cudaError_t launch_wait_probe(int32_t* status, int polls, cudaStream_t st);
 
 }  // namespace prism
