@@ -9,8 +9,11 @@ Laplacian and directional continuity) inside mask-cropped 16^3 patches. One step
 MSE, hand-written adjoint, priors and the Adam update of every parameter, in the
 fused persistent kernel replayed from a CUDA graph.
 
-Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle on a
-bounded sample of the same workload instead.
+Under torchrun with N ranks (one per GPU) the brain's 16^3 patches are split across the
+ranks, balanced by voxel count, each rank fitting its share with the whole brain's |M| as
+the normaliser and no collective on the data path (strong scaling: the work is one brain
+whatever N is). Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
 """
 import argparse
 import json
@@ -40,12 +43,24 @@ FLOPS_PER_PAIR = 17 + 28 * K_FIB
 # Pairs of b = 0 measurements (the kernel's table starts with them) need no fiber terms:
 # r = y - S0 sum(f) and r^2 (two multiply-adds) and the running sum of r (one add).
 FLOPS_PER_B0_PAIR = 5
-# DRAM bytes per voxel-iteration of the fused kernel (read + write), from an ncu capture of
-# this kernel version on the scaled brain (212,900 voxels: 396.0 and 392.1 MB in two launches); traffic grows
-# in proportion to the voxels. Must return to None when the kernel changes.
-TRAFFIC_BYTES_PER_VOXEL_ITER = 1851.0
-# FP32 peak: 152 SMs x 128 lanes x 2 flops x 2070 MHz (maximum SM clock).
-PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# DRAM bytes per voxel-iteration of the fused kernel (read + write) from an ncu capture of the
+# scaled brain (traffic grows in proportion to the voxels), valid only for the kernel sources
+# whose SHA-256 is TRAFFIC_SOURCES_SHA256: any other hash reports the traffic as null.
+TRAFFIC_BYTES_PER_VOXEL_ITER = None
+TRAFFIC_SOURCES_SHA256 = None
+FUSED_SOURCES = ("prism_kernels.cuh", "prism_device.cuh", "prism_kset.cuh", "bessel_fit.h", "prism_k3.cu")
+# FP32 lanes per SM on GB300 (4 sub-partitions x 32); the peak multiplies them by the device's
+# SM count, 2 flops per fused multiply-add and the maximum SM clock seen by nvidia-smi.
+FP32_LANES_PER_SM = 128
+
+
+def fused_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for name in FUSED_SOURCES:
+        with open(os.path.join(ROOT, "paper_2604_00250_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 
 
 def dist_env():
@@ -184,7 +199,7 @@ def run_reference(args):
     sample = f"one 16^3 patch ({nvox} voxels) of the {V}-voxel brain per step"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": cfg_dict(V, {"sample": sample}),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -202,6 +217,7 @@ def run_ours(args):
     if world > 1:
         dist.init_process_group("nccl", init_method="env://")
     import paper_2604_00250_gb300 as prism
+    from paper_2604_00250_gb300 import shard
     dev = torch.device("cuda", local)
 
     def barrier():
@@ -216,11 +232,18 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    vol = make_brain(args.seed + rank, "cuda", args.brain_scale)
-    V = vol.n_vox
+    # one brain; with N > 1 ranks each fits its share of the 16^3 patches (occupancy-balanced,
+    # the whole brain's |M| as the normaliser) and no data crosses ranks while fitting
+    vol = make_brain(args.seed, "cuda", args.brain_scale)
+    V_all = vol.n_vox
     N = vol.n_meas
-    sig_dev = torch.as_tensor(vol.signal, device=dev)
-    vdev = types.SimpleNamespace(mask=vol.mask, signal=sig_dev, bvals=vol.bvals, bvecs=vol.bvecs, init=None)
+    whole = types.SimpleNamespace(mask=vol.mask, signal=vol.signal, bvals=vol.bvals, bvecs=vol.bvecs, init=None,
+                                  norm_count=0)
+    part = shard.shard_volume(whole, 16, rank, world)[0] if world > 1 else whole
+    V = int(np.count_nonzero(part.mask))
+    sig_dev = torch.as_tensor(part.signal, device=dev)
+    vdev = types.SimpleNamespace(mask=part.mask, signal=sig_dev, bvals=vol.bvals, bvecs=vol.bvecs, init=None,
+                                 norm_count=part.norm_count)
     opts = prism.options(K=K_FIB, loss="mse", patch_dim=16, fused=1, use_graph=1, autotune=int(args.autotune),
                          threads_per_voxel=args.threads_per_voxel, **PRIORS)
     f = prism.Fitter([vdev], opts)
@@ -243,12 +266,20 @@ def run_ours(args):
     f.sync()
     ms_total = max_over_ranks(e0.elapsed_time(e1))
     ms_step = ms_total / args.steps
-    value = world * V * args.steps / (ms_total / 1e3)
+    value = V_all * args.steps / (ms_total / 1e3)
     # ---- live per-kernel timing (CUDA events around each kernel class, no graph)
     prof = f.profile(min(args.steps, 50))
     fused_ms = prof["fused_ms"]
     nb0 = 2 * (int(np.count_nonzero(np.asarray(vol.bvals) == 0)) // 2)
     achieved = V * ((N - nb0) * FLOPS_PER_PAIR + nb0 * FLOPS_PER_B0_PAIR) / (fused_ms / 1e3) / 1e12
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max_mhz = ck.get("sm_max_mhz") or 2070.0
+    peak = n_sm * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    peak_at_median = n_sm * FP32_LANES_PER_SM * 2 * ck["sm_mhz"] * 1e6 / 1e12 if ck.get("sm_mhz") else None
+    ffma_measured = prism.microbench("ffma") / 1e12
+    sha = fused_sources_sha256()
+    traffic = (V * TRAFFIC_BYTES_PER_VOXEL_ITER
+               if TRAFFIC_BYTES_PER_VOXEL_ITER and sha == TRAFFIC_SOURCES_SHA256 else None)
     loss_last = float(f.loss()[0])
     tile = f.shape()
     f.close()
@@ -267,15 +298,16 @@ def run_ours(args):
         u1.synchronize()
         fu.sync()
         ms_u = max_over_ranks(u0.elapsed_time(u1)) / n_u
-        unfused = {"value": world * V / (ms_u / 1e3), "ms_per_step": ms_u, "steps": n_u,
+        unfused = {"value": V_all / (ms_u / 1e3), "ms_per_step": ms_u, "steps": n_u,
                    "launches_per_step": None}
         fu.close()
     # ---- end to end through prism_fit with HOST buffers (copies inside the timed region)
     e2e = None
     if not args.no_e2e:
-        sig_host = torch.empty(vol.signal.shape, dtype=torch.float32, pin_memory=True)
-        sig_host.copy_(torch.as_tensor(vol.signal))
-        vhost = types.SimpleNamespace(mask=vol.mask, signal=sig_host, bvals=vol.bvals, bvecs=vol.bvecs, init=None)
+        sig_host = torch.empty(tuple(part.signal.shape), dtype=torch.float32, pin_memory=True)
+        sig_host.copy_(torch.as_tensor(part.signal))
+        vhost = types.SimpleNamespace(mask=part.mask, signal=sig_host, bvals=vol.bvals, bvecs=vol.bvecs, init=None,
+                                      norm_count=part.norm_count)
         n_e2e = args.e2e_iters
         out = torch.empty((V, 4 * K_FIB + 5), dtype=torch.float32, pin_memory=True)
         import ctypes
@@ -294,12 +326,13 @@ def run_ours(args):
                                      loss_out.ctypes.data, prism.MEM_HOST, ctypes.c_void_p(stream.cuda_stream)))
             torch.cuda.synchronize()
             runs.append(max_over_ranks(time.perf_counter() - t0))
-        dt = min(runs)
+        dt = float(np.median(runs))
         h2d = sig_host.numel() * 4 + vol.mask.size + N * 16
         d2h = out.numel() * 4 + 8
-        e2e = {"value": world * V * n_e2e / dt, "unit": UNIT, "h2d_bytes_per_step": h2d / n_e2e,
+        e2e = {"value": V_all * n_e2e / dt, "unit": UNIT, "h2d_bytes_per_step": h2d / n_e2e,
                "d2h_bytes_per_step": d2h / n_e2e, "iterations": n_e2e, "seconds": dt,
-               "seconds_all_calls": [round(r, 4) for r in runs], "timing": "wall clock, fastest of 3 calls",
+               "value_fastest": V_all * n_e2e / min(runs), "seconds_fastest": min(runs),
+               "seconds_all_calls": [round(r, 4) for r in runs], "timing": "wall clock, median of 3 calls",
                "call": "prism_fit (init + iterations + readout), pinned host signal and parameters"}
     # ---- CPU baseline: the FP64 oracle on a bounded sample (rank 0, N = 1 only)
     cpu = None
@@ -323,16 +356,22 @@ def run_ours(args):
     launches = 1 + (1 if PRIORS["lam_sp"] > 0 else 0) + (1 if tile["threads_per_voxel"] > 1 else 0)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "strong",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": cfg_dict(V, {"timing": "CUDA events, graph replay, max over ranks",
+                "config": cfg_dict(V_all, {"timing": "CUDA events, graph replay, max over ranks",
+                                           "partition": (f"{world} ranks, 16^3 patches balanced by voxel count, "
+                                                         f"rank 0 fits {V} voxels" if world > 1 else "one GPU"),
                                        "brain_scale": args.brain_scale, "launch": tile}),
-                "roofline": {"bound": "alu", "achieved": achieved, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
-                             "frac": achieved / PEAK_FP32_TFLOPS,
-                             "traffic": (V * TRAFFIC_BYTES_PER_VOXEL_ITER if TRAFFIC_BYTES_PER_VOXEL_ITER else None),
+                "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                             "frac": achieved / peak, "traffic": traffic,
                              "traffic_unit": "bytes per launch (ncu dram read + write, scaled capture)",
                              "kernel": "k_iter_fused", "kernel_ms": fused_ms,
-                             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
+                             "peak_source": f"derived: {n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                                            f"{sm_max_mhz:.0f} MHz (maximum SM clock sampled)",
+                             "peak_at_median_clock": peak_at_median,
+                             "ffma_microbench": ffma_measured,
+                             "frac_of_ffma_microbench": achieved / ffma_measured,
+                             "fused_sources_sha256": sha},
                 "unfused": unfused,
                 "speedup_vs_unfused": (value / unfused["value"]) if unfused else None,
                 "profile_ms": prof, "final_loss": loss_last,
@@ -469,7 +508,8 @@ def run_disco(args):
 def run_crossing(args):
     """Quality of the fit on the crossing-fiber benchmark layout (16 angles + single-fiber
     controls, N = 193) at each SNR and both data terms: one JSON line per run with the
-    best-match angular error per angle, overall, recall and F1 (readings R20, R31)."""
+    best-match angular error per angle, overall, recall and F1 (Sec. 3 "Tracking & metrics";
+    peaks are fibers with at least 15 % of the white-matter fraction)."""
     import torch
     import phantoms as P
     import paper_2604_00250_gb300 as prism

@@ -87,7 +87,7 @@ def _vol(mask, bvals=None, bvecs=None):
 
 @pytest.mark.parametrize("case,code", [
     ("k_out_of_range", 1), ("empty_mask", 2), ("no_b0", 2), ("non_unit_bvec", 1), ("negative_b", 1),
-    ("bad_patch", 1), ("bad_tpv", 1), ("negative_lambda", 1),
+    ("bad_patch", 1), ("bad_tpv", 1), ("negative_lambda", 1), ("norm_count_below_mask", 2),
 ])
 def test_validation_errors(prism, case, code):
     m = np.ones((2, 2, 2), np.uint8)
@@ -109,6 +109,8 @@ def test_validation_errors(prism, case, code):
         kw = dict(threads_per_voxel=3)
     elif case == "negative_lambda":
         kw = dict(lam_rep=-1.0)
+    elif case == "norm_count_below_mask":
+        vol.norm_count = 7               # the mask holds 8 voxels
     with pytest.raises(prism.PrismError) as e:
         prism.Fitter([vol], prism.options(**kw))
     assert e.value.code == code
