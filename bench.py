@@ -36,12 +36,18 @@ WORKLOAD = "hcp_shaped_brain_145x174x145_ellipsoid_mask_N288_K3_mse_patch16"
 K_FIB = 3
 PRIORS = dict(lam_rep=0.01, lam_sparse=0.02, lam_sp=0.01, lam_dir=0.005)
 
-# FP32 floating-point operations per (voxel, measurement) pair of the fused kernel's hot
-# loop on this workload (packed two-measurement path: MSE, no calibration), fused
-# multiply-add = 2: 17 per measurement + 28 per fiber.
+# FP32 floating-point operations per (voxel, measurement) pair of the fused kernel's loop on
+# this workload (MSE, no calibration), fused multiply-add = 2.
+# Shell loop (every shell of the scheme even): per fiber 27 -- scaled cosine c' = d' . g 5,
+# exponent arguments 2 + 2, f_in e1 + (1 - f_in) p 1, T 2, the two adjoint sums 4, dE/dc
+# factor 3, its product with r c' 2, the direction sum 6 -- and per measurement 5 (residual 2,
+# its square 2, the shell's sum of r 1); the isotropic terms are formed once per shell.
+FLOPS_PER_PAIR_SHELL = 5 + 27 * K_FIB
+# Per-measurement loop: 17 per measurement (isotropic mixture 5, residual 2, its square 2,
+# isotropic adjoint 6, two derivative constants 2) + 28 per fiber.
 FLOPS_PER_PAIR = 17 + 28 * K_FIB
-# Pairs of b = 0 measurements (the kernel's table starts with them) need no fiber terms:
-# r = y - S0 sum(f) and r^2 (two multiply-adds) and the running sum of r (one add).
+# Measurements with b = 0 (leading the table) need no fiber terms: r = y - S0 sum(f) and r^2
+# (two multiply-adds) and the running sum of r (one add).
 FLOPS_PER_B0_PAIR = 5
 # DRAM bytes per voxel-iteration of the fused kernel (read + write) from an ncu capture of the
 # scaled brain (traffic grows in proportion to the voxels), valid only for the kernel sources
@@ -271,7 +277,9 @@ def run_ours(args):
     prof = f.profile(min(args.steps, 50))
     fused_ms = prof["fused_ms"]
     nb0 = 2 * (int(np.count_nonzero(np.asarray(vol.bvals) == 0)) // 2)
-    achieved = V * ((N - nb0) * FLOPS_PER_PAIR + nb0 * FLOPS_PER_B0_PAIR) / (fused_ms / 1e3) / 1e12
+    shape = f.shape()
+    per_pair = FLOPS_PER_PAIR_SHELL if shape["shell_loop"] else FLOPS_PER_PAIR
+    achieved = V * ((N - nb0) * per_pair + nb0 * FLOPS_PER_B0_PAIR) / (fused_ms / 1e3) / 1e12
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max_mhz = ck.get("sm_max_mhz") or 2070.0
     peak = n_sm * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
@@ -364,6 +372,7 @@ def run_ours(args):
                                        "brain_scale": args.brain_scale, "launch": tile}),
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                              "frac": achieved / peak, "traffic": traffic,
+                             "flops_per_voxel_iteration": (N - nb0) * per_pair + nb0 * FLOPS_PER_B0_PAIR,
                              "traffic_unit": "bytes per launch (ncu dram read + write, scaled capture)",
                              "kernel": "k_iter_fused", "kernel_ms": fused_ms,
                              "peak_source": f"derived: {n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "

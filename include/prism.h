@@ -109,9 +109,15 @@ typedef struct prism_options {
                                 128-voxel tiles come to 0.75-1.25 waves of the fused kernel's
                                 resident CTAs (then 4); prism_get_shape reports the choice */
   int32_t cta_threads;    /* plain path: 128 or 256 threads per CTA; 0 = automatic (the fused kernel uses 128) */
-  int32_t autotune;       /* 1: time the candidate tile shapes at init and keep the fastest */
+  int32_t autotune;       /* 1: time the candidate launch shapes at init and keep the fastest: lanes
+                             per voxel 1 / 4 / 16 (or the forced value) and, with one lane, the shell
+                             loop or the per-measurement loop; above about 311k voxels on a bounded
+                             sample of each volume's fullest patches */
   int32_t seed;           /* seed of the default initialisation (init == NULL) */
-  int32_t reserved[4];
+  int32_t shells;         /* fused kernel, one thread per voxel, MSE, no calibration, K <= 3: 0 = take
+                             the shell loop (per b-value shell work done once; needs every shell of
+                             every volume to hold an even number of measurements), -1 = never */
+  int32_t reserved[3];
 } prism_options;
 
 /* Fills `opt` with the paper's defaults (MSE, K = 3, no calibration, repulsion + sparsity). */
@@ -154,12 +160,14 @@ int prism_info(const prism_handle* h, int64_t* n_vox, int32_t* n_groups, int32_t
 
 /*
  * Launch shape the handle runs with: lanes per voxel (1, 4 or 16; chosen at init from the
- * voxel count unless prism_options.threads_per_voxel forces one), voxels per tile, and CTAs of
- * the persistent fused kernel (0 for a plain handle). Any output pointer may be NULL. The paper
+ * voxel count unless prism_options.threads_per_voxel forces one), voxels per tile, CTAs of
+ * the persistent fused kernel (0 for a plain handle) and whether the fused kernel takes the
+ * shell loop (1) or the per-measurement loop (0). Any output pointer may be NULL. The paper
  * has no counterpart: the shape is this implementation's. Errors: PRISM_E_INVALID_ARG for a
  * NULL handle.
  */
-int prism_get_shape(const prism_handle* h, int32_t* threads_per_voxel, int32_t* tile_voxels, int32_t* fused_grid);
+int prism_get_shape(const prism_handle* h, int32_t* threads_per_voxel, int32_t* tile_voxels, int32_t* fused_grid,
+                    int32_t* shell_loop);
 
 /* Raw parameters [V][Q] in mask order, to/from host or device memory (per `mem`). */
 int prism_get_params(prism_handle* h, float* out, int32_t mem, void* stream);

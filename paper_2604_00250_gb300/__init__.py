@@ -319,10 +319,11 @@ class Fitter:
         return gth, gg
 
     def shape(self):
-        """Launch shape: lanes per voxel, voxels per tile, CTAs of the fused kernel."""
-        tpv, tv, grid = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
-        _lib.check(self._lib.prism_get_shape(self._h, ctypes.byref(tpv), ctypes.byref(tv), ctypes.byref(grid)))
-        return dict(threads_per_voxel=tpv.value, tile_voxels=tv.value, fused_grid=grid.value)
+        """Launch shape: lanes per voxel, voxels per tile, CTAs of the fused kernel, shell loop."""
+        tpv, tv, grid, sh = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _lib.check(self._lib.prism_get_shape(self._h, ctypes.byref(tpv), ctypes.byref(tv), ctypes.byref(grid),
+                                             ctypes.byref(sh)))
+        return dict(threads_per_voxel=tpv.value, tile_voxels=tv.value, fused_grid=grid.value, shell_loop=sh.value)
 
     def profile(self, n_iters=10, stream=None):
         """Average ms per iteration: fused kernel, prior preparation, group kernels, total."""

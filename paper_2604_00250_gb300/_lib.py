@@ -53,7 +53,8 @@ class Options(ctypes.Structure):
         ("rprop_step_min", ctypes.c_float), ("rprop_step_max", ctypes.c_float),
         ("fused", ctypes.c_int32), ("use_graph", ctypes.c_int32),
         ("threads_per_voxel", ctypes.c_int32), ("cta_threads", ctypes.c_int32),
-        ("autotune", ctypes.c_int32), ("seed", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4),
+        ("autotune", ctypes.c_int32), ("seed", ctypes.c_int32), ("shells", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 3),
     ]
 
 
@@ -78,7 +79,7 @@ def load():
         "prism_sync": (ctypes.c_int, [vp, vp]),
         "prism_wait_probe": (ctypes.c_int, [vp, i32, vp]),
         "prism_info": (ctypes.c_int, [vp, P(i64), P(i32), P(i32), P(i64), P(i64)]),
-        "prism_get_shape": (ctypes.c_int, [vp, P(i32), P(i32), P(i32)]),
+        "prism_get_shape": (ctypes.c_int, [vp, P(i32), P(i32), P(i32), P(i32)]),
         "prism_get_params": (ctypes.c_int, [vp, vp, i32, vp]),
         "prism_set_params": (ctypes.c_int, [vp, vp, i32, vp]),
         "prism_group_layout": (ctypes.c_int, [vp, vp]),

@@ -107,6 +107,13 @@ struct prism_handle {
   MeasRow* d_table = nullptr;
   MeasPair* d_table2 = nullptr;
   int64_t tab2_pairs = 0;
+  // shell loop: per-group gradient rows and shells (host copies built by the plan)
+  std::vector<float> gtab;
+  std::vector<ShellRun> runs;
+  bool shells_even = true;             // every group's shells hold an even number of measurements
+  bool shell = false;                  // the fused kernel takes the shell loop
+  float* d_gtab = nullptr;
+  ShellRun* d_runs = nullptr;
   double *d_tile_red = nullptr, *d_part2 = nullptr, *d_gred = nullptr, *d_gloss = nullptr;
   double* d_bscratch = nullptr;      // bias-gradient partial contractions (calibration only)
   int64_t* d_bs_off = nullptr;       // [G][2] offsets into d_bscratch
@@ -216,6 +223,7 @@ int validate_options(const prism_options& o) {
     return fail(PRISM_E_INVALID_ARG, "Rprop needs 0 < eta_minus < 1 < eta_plus and 0 < step_min <= lr <= step_max");
   if (o.threads_per_voxel != 0 && o.threads_per_voxel != 1 && o.threads_per_voxel != 4 && o.threads_per_voxel != 16)
     return fail(PRISM_E_INVALID_ARG, "threads_per_voxel must be 0, 1, 4 or 16");
+  if (o.shells != 0 && o.shells != -1) return fail(PRISM_E_INVALID_ARG, "shells must be 0 (automatic) or -1 (off)");
   if (o.cta_threads != 0 && o.cta_threads != 128 && o.cta_threads != 256)
     return fail(PRISM_E_INVALID_ARG, "cta_threads must be 0, 128 or 256");
   return PRISM_OK;
@@ -269,6 +277,8 @@ void fill_args(prism_handle* h) {
   a.vflag = h->d_vflag;
   a.table = h->d_table;
   a.table2 = h->d_table2;
+  a.gtab = h->d_gtab;
+  a.runs = h->d_runs;
   a.gparams = h->d_gparams;
   a.gU = h->d_gU;
   a.tile_ab = h->d_tile_ab;
@@ -345,8 +355,8 @@ void fill_args(prism_handle* h) {
 int enqueue_fused_iter(prism_handle* h, cudaStream_t st) {
   const IterArgs& a = h->ia;
   if (h->opt.lam_sp > 0.f) CK(h->ks->prior_prep(a, 0, h->ntiles, st));
-  if (h->nb && h->TPV > 1) CK(h->ks->prior_grad(a, 0, h->ntiles, st));
-  CK(h->ks->fused(a, h->opt.loss, h->cal ? 1 : 0, h->TPV, h->fused_grid, h->NT, h->fused_smem, st));
+  if (h->nb) CK(h->ks->prior_grad(a, 0, h->ntiles, st));
+  CK(h->ks->fused(a, h->opt.loss, h->cal ? 1 : 0, h->TPV, h->shell ? 1 : 0, h->fused_grid, h->NT, h->fused_smem, st));
   if (h->cal) {   // without calibration the fused kernel's last CTA finalises the groups
     CK(launch_bias_grad(a, h->ga, st));
     CK(launch_group_reduce(a, h->ga, 1 | 2, st));
@@ -395,25 +405,57 @@ int capture_graph(prism_handle* h, int iters, cudaGraphExec_t* out) {
 
 // Host-side plan of volumes -> patches -> tiles, neighbours and flags.
 // Internal measurement order of one group, appended to `order` (table position -> the
-// caller's index). Without calibration the b = 0 measurements come first (stable), so that
-// the packed path can take their pairs without the fiber terms (every E of Eqs. 4-5 is 1 at
-// b = 0); with calibration, whose alpha_n / beta_n are indexed by measurement, the order is
-// the caller's. Returns the number of leading pairs whose two measurements have b = 0.
+// caller's index). Without calibration the measurements are sorted by b-value (stable): the
+// b = 0 ones come first, so that the packed path can take their pairs without the fiber terms
+// (every E of Eqs. 4-5 is 1 at b = 0), and equal b-values form runs (shells) for the shell
+// loop. With calibration, whose alpha_n / beta_n are indexed by measurement, the order is the
+// caller's. Returns the number of leading pairs whose two measurements have b = 0.
 static int32_t meas_order(const prism_volume& v, bool cal, std::vector<int32_t>& order) {
   const int N = v.n_meas;
   if (cal) {
     for (int n = 0; n < N; ++n) order.push_back(n);
     return 0;
   }
+  std::vector<int32_t> idx(N);
+  for (int n = 0; n < N; ++n) idx[n] = n;
+  std::stable_sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) { return v.bvals[a] < v.bvals[b]; });
   int nz = 0;
-  for (int n = 0; n < N; ++n)
-    if (v.bvals[n] == 0.f) {
-      order.push_back(n);
-      ++nz;
-    }
-  for (int n = 0; n < N; ++n)
-    if (v.bvals[n] != 0.f) order.push_back(n);
+  for (int n = 0; n < N; ++n) nz += v.bvals[n] == 0.f;
+  order.insert(order.end(), idx.begin(), idx.end());
   return nz / 2;
+}
+
+// Shells of one group in table order (runs of equal b-value) with the constants of the
+// shell loop (ShellRun); false when a shell holds an odd number of measurements (a pair would
+// straddle two shells) or there are more than kMaxRuns shells.
+static bool shell_runs(const prism_volume& v, const int32_t* ord, std::vector<ShellRun>& runs) {
+  const int N = v.n_meas;
+  const double L2E = 1.4426950408889634, dpar = 1.7e-3, dperp = 0.4e-3;   // Eq. 5, mm^2/s
+  bool ok = true;
+  int n0 = 0, nr = 0;
+  while (n0 < N) {
+    const float b = v.bvals[ord[n0]];
+    int n1 = n0 + 1;
+    while (n1 < N && v.bvals[ord[n1]] == b) ++n1;
+    if ((n1 - n0) % 2 != 0) ok = false;
+    ShellRun r{};
+    r.p0 = n0 / 2;
+    r.p1 = n1 / 2;
+    r.b0 = (b == 0.f) ? 1 : 0;
+    const double bd = b;
+    r.ecsf = static_cast<float>(std::exp(-bd * 3.0e-3));   // Eq. 4
+    r.egm = static_cast<float>(std::exp(-bd * 0.9e-3));
+    r.eres = static_cast<float>(std::exp(-bd * 0.2e-3));
+    r.nbperp = static_cast<float>(-bd * dperp * L2E);
+    const double s = std::sqrt(bd * dpar * L2E);
+    r.s = static_cast<float>(s);
+    r.ap = (s > 0.0) ? static_cast<float>(-2.0 * bd * dpar / s) : 0.f;
+    r.bp = (s > 0.0) ? static_cast<float>(2.0 * bd * (dperp - dpar) / s) : 0.f;
+    runs.push_back(r);
+    ++nr;
+    n0 = n1;
+  }
+  return ok && nr <= kMaxRuns;
 }
 
 // Runs fn(begin, end) over [0, n) split into contiguous chunks on up to 16 host threads (one
@@ -542,6 +584,19 @@ int build_plan(prism_handle* h, const prism_volume* vols, int n_vols, Plan& pl) 
     gr.calib = h->cal ? 1 : 0;
     gr.table_off = static_cast<int32_t>(tab);
     gr.nb0p = meas_order(v, h->cal, h->order);
+    {
+      // shells and gradient rows of the group's table order (shell loop)
+      const int32_t* ord = h->order.data() + tab;
+      gr.run_off = static_cast<int32_t>(h->runs.size());
+      if (!shell_runs(v, ord, h->runs)) h->shells_even = false;
+      gr.n_runs = static_cast<int32_t>(h->runs.size()) - gr.run_off;
+      const int NPg = (v.n_meas + 3) & ~3;
+      gr.gtab_off = static_cast<int32_t>(h->gtab.size());
+      h->gtab.resize(h->gtab.size() + 3 * static_cast<size_t>(NPg), 0.f);
+      float* gt = h->gtab.data() + gr.gtab_off;
+      for (int n = 0; n < v.n_meas; ++n)
+        for (int c = 0; c < 3; ++c) gt[c * NPg + n] = v.bvecs[3 * ord[n] + c];
+    }
     tab += v.n_meas;
     gr.table2_off = static_cast<int32_t>(h->tab2_pairs);
     h->tab2_pairs += ((v.n_meas + 3) & ~3) / 2;
@@ -708,7 +763,7 @@ int init_impl(prism_handle* h, const prism_volume* vols, int n_vols, const std::
   RC(h->alloc(&h->d_xf, 2 * static_cast<size_t>(h->XF) * Vp));
   RC(h->alloc(&h->d_hsp, static_cast<size_t>(h->K + 3) * Vp));
   RC(h->alloc(&h->d_lp, Vp));
-  const size_t pg_len = (h->nb && o.fused && h->TPV > 1) ? static_cast<size_t>(4 * h->K + 4) * Vp : 1;
+  const size_t pg_len = (h->nb && o.fused) ? static_cast<size_t>(4 * h->K + 4) * Vp : 1;
   RC(h->alloc(&h->d_pg, pg_len));
   CK(cudaMemsetAsync(h->d_pg, 0, sizeof(float) * pg_len, st));
   RC(h->alloc(&h->d_gU, Vp));
@@ -720,6 +775,8 @@ int init_impl(prism_handle* h, const prism_volume* vols, int n_vols, const std::
   RC(h->alloc(&h->d_table, h->tab_rows));
   RC(h->alloc(&h->d_table2, h->tab2_pairs));
   CK(cudaMemsetAsync(h->d_table2, 0, sizeof(MeasPair) * h->tab2_pairs, st));
+  RC(h->alloc(&h->d_gtab, h->gtab.size()));
+  RC(h->alloc(&h->d_runs, h->runs.size()));
   RC(h->alloc(&h->d_gparams, h->GP));
   RC(h->alloc(&h->d_gm, h->GP));
   RC(h->alloc(&h->d_gv, h->GP));
@@ -797,6 +854,8 @@ int init_impl(prism_handle* h, const prism_volume* vols, int n_vols, const std::
                       Vp, h->TV, h->opt.connectivity, h->d_vox_of_slot, h->d_vcoord, h->d_vflag, h->d_nbr, st));
   RC(upload(h->d_row_off, pl.row_off, st));
   RC(upload(h->d_order, h->order, st));
+  RC(upload(h->d_gtab, h->gtab, st));
+  RC(upload(h->d_runs, h->runs, st));
   RC(upload(h->d_split_off, split_off, st));
   fill_args(h);
   // per volume: b0 statistics, packing, table, sigma, parameters
@@ -879,15 +938,22 @@ int init_impl(prism_handle* h, const prism_volume* vols, int n_vols, const std::
   CK(launch_adam_constants(h->ia, st));
   // launch geometry of the fused kernel
   const int NW = h->NT / 32;
-  h->fused_smem = static_cast<size_t>(h->Nmax) * sizeof(MeasRow) +
-                  static_cast<size_t>(kStages) * kChunk * (kFusedThreads / h->TPV) * sizeof(float) +
-                  (h->cal ? kNGrid * sizeof(float) + static_cast<size_t>(NW) * 2 * h->Nmax * sizeof(float) : 0);
+  h->shell = o.fused && !h->cal && o.loss == PRISM_LOSS_MSE && h->TPV == 1 && o.K <= 3 && h->shells_even &&
+             o.shells == 0;
+  const size_t ring = static_cast<size_t>(kStages) * kChunk * (kFusedThreads / h->TPV) * sizeof(float);
+  if (h->shell) {
+    h->fused_smem = 3 * static_cast<size_t>(h->Nmax) * sizeof(float) + kMaxRuns * sizeof(ShellRun) +
+                    static_cast<size_t>(3 * o.K + 9) * kFusedThreads * sizeof(float) + ring;
+  } else {
+    h->fused_smem = static_cast<size_t>(h->Nmax) * sizeof(MeasRow) + ring +
+                    (h->cal ? kNGrid * sizeof(float) + static_cast<size_t>(NW) * 2 * h->Nmax * sizeof(float) : 0);
+  }
   h->adj_smem = h->cal ? static_cast<size_t>(NW) * 2 * h->Nmax * sizeof(float) : 0;
   if (o.fused) {
     int dev = 0, sms = 0, bps = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    CK(h->ks->fused_occupancy(o.loss, h->cal ? 1 : 0, h->TPV, h->NT, h->fused_smem, &bps));
+    CK(h->ks->fused_occupancy(o.loss, h->cal ? 1 : 0, h->TPV, h->shell ? 1 : 0, h->NT, h->fused_smem, &bps));
     if (bps < 1) return fail(PRISM_E_CUDA, "fused kernel does not fit on an SM");
     h->fused_grid = std::max(1, std::min(h->ntiles, sms * bps));
   }
@@ -950,6 +1016,22 @@ int build_graphs(prism_handle* h) {
   return PRISM_OK;
 }
 
+// A device buffer freed when it goes out of scope.
+struct DevTmp {
+  void* p = nullptr;
+  DevTmp() = default;
+  DevTmp(const DevTmp&) = delete;
+  DevTmp& operator=(const DevTmp&) = delete;
+  DevTmp(DevTmp&& o) noexcept : p(o.p) { o.p = nullptr; }
+  ~DevTmp() {
+    if (p) cudaFree(p);
+  }
+  template <typename T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
 int create_handle(const prism_volume* vols, int n_vols, const std::vector<int64_t>& counts, const prism_options& o,
                   int tpv, int nt, cudaStream_t st, prism_handle** out) {
   std::unique_ptr<prism_handle> h(new (std::nothrow) prism_handle());
@@ -961,6 +1043,149 @@ int create_handle(const prism_volume* vols, int n_vols, const std::vector<int64_
   if (o.fused && o.use_graph) RC(build_graphs(h.get()));
   *out = h.release();
   return PRISM_OK;
+}
+
+// Autotuning of the launch shape (prism_options.autotune): lanes per voxel (1, 4 or 16, or the
+// forced value) and, with one lane, the shell loop or the per-measurement loop, each timed for a
+// few fused iterations on the problem itself or, above kTuneVoxels, on a bounded sample of it:
+// per volume its fullest patches in proportion to its voxels (whole patches, the volume's |M|
+// as normaliser), about four waves of 128-voxel tiles of a GB300's resident CTAs. The voxels
+// per tile (128 / lanes) and the ring depth are fixed by the compiled kernels.
+constexpr int64_t kTuneVoxels = 4LL * 152 * 4 * 128;
+
+struct TuneSample {
+  std::vector<prism_volume> vols;
+  std::vector<std::vector<uint8_t>> masks;
+  std::vector<std::vector<float>> host_sig;
+  std::vector<DevTmp> dev_sig, dev_rows;
+  std::vector<int64_t> counts;
+};
+
+int tune_sample(const prism_volume* vols, int n_vols, const std::vector<int64_t>& counts, int P, int64_t budget,
+                cudaStream_t st, TuneSample& S) {
+  int64_t V = 0;
+  for (int64_t c : counts) V += c;
+  S.vols.assign(vols, vols + n_vols);
+  S.masks.resize(n_vols);
+  S.host_sig.resize(n_vols);
+  S.dev_sig.resize(n_vols);
+  S.dev_rows.resize(n_vols);
+  S.counts.assign(n_vols, 0);
+  for (int g = 0; g < n_vols; ++g) {
+    const prism_volume& v = vols[g];
+    const int64_t ng = static_cast<int64_t>(v.nx) * v.ny * v.nz;
+    const int px = (v.nx + P - 1) / P, py = (v.ny + P - 1) / P, pz = (v.nz + P - 1) / P;
+    std::vector<int32_t> pcount(static_cast<size_t>(px) * py * pz, 0);
+    auto pid_of = [&](int64_t i) {
+      const int x = static_cast<int>(i / (static_cast<int64_t>(v.ny) * v.nz)), y = static_cast<int>((i / v.nz) % v.ny),
+                z = static_cast<int>(i % v.nz);
+      return (static_cast<int64_t>(x / P) * py + y / P) * pz + z / P;
+    };
+    for (int64_t i = 0; i < ng; ++i)
+      if (v.mask[i]) ++pcount[pid_of(i)];
+    std::vector<int32_t> order(pcount.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = static_cast<int32_t>(i);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return pcount[a] > pcount[b]; });
+    const int64_t quota = std::max<int64_t>(1, budget * counts[g] / std::max<int64_t>(V, 1));
+    std::vector<uint8_t> keep(pcount.size(), 0);
+    int64_t got = 0;
+    for (int32_t p : order) {
+      if (got >= quota || pcount[p] == 0) break;
+      keep[p] = 1;
+      got += pcount[p];
+    }
+    S.masks[g].assign(v.mask, v.mask + ng);
+    std::vector<int64_t> rows;
+    int64_t r = 0;
+    for (int64_t i = 0; i < ng; ++i) {
+      if (!v.mask[i]) continue;
+      if (keep[pid_of(i)]) rows.push_back(r);
+      else S.masks[g][i] = 0;
+      ++r;
+    }
+    const int N = v.n_meas;
+    const int64_t n = static_cast<int64_t>(rows.size());
+    prism_volume& pv = S.vols[g];
+    pv.mask = S.masks[g].data();
+    pv.init = nullptr;
+    pv.norm_count = v.norm_count > 0 ? v.norm_count : static_cast<int32_t>(counts[g]);
+    S.counts[g] = n;
+    if (v.mem == PRISM_MEM_HOST) {
+      S.host_sig[g].resize(static_cast<size_t>(n) * N);
+      for (int64_t i = 0; i < n; ++i)
+        std::memcpy(S.host_sig[g].data() + i * N, v.signal + rows[i] * N, sizeof(float) * N);
+      pv.signal = S.host_sig[g].data();
+    } else {
+      CK(cudaMalloc(&S.dev_rows[g].p, sizeof(int64_t) * n));
+      CK(cudaMemcpyAsync(S.dev_rows[g].p, rows.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, st));
+      CK(cudaMalloc(&S.dev_sig[g].p, sizeof(float) * n * N));
+      CK(launch_gather_rows(v.signal, S.dev_rows[g].as<int64_t>(), n, N, S.dev_sig[g].as<float>(), st));
+      pv.signal = S.dev_sig[g].as<float>();
+    }
+  }
+  CK(cudaStreamSynchronize(st));
+  return PRISM_OK;
+}
+
+void autotune_shape(const prism_volume* vols, int n_vols, const std::vector<int64_t>& counts, const prism_options& o,
+                    cudaStream_t st, int* tpv, int* shells) {
+  int64_t V = 0;
+  for (int64_t c : counts) V += c;
+  TuneSample S;
+  const prism_volume* tv = vols;
+  const std::vector<int64_t>* tc = &counts;
+  if (V > kTuneVoxels) {
+    if (tune_sample(vols, n_vols, counts, o.patch_dim, kTuneVoxels, st, S) != PRISM_OK) {
+      g_err.clear();
+      return;
+    }
+    tv = S.vols.data();
+    tc = &S.counts;
+  }
+  prism_options oc = o;
+  oc.use_graph = 0;
+  oc.autotune = 0;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return;
+  }
+  float best = 1e30f;
+  const int lanes[3] = {1, 4, 16};
+  for (int lane : lanes) {
+    if (o.threads_per_voxel && lane != o.threads_per_voxel) continue;
+    for (int sh : {0, -1}) {
+      if (o.shells == -1 && sh == 0) continue;
+      oc.shells = sh;
+      prism_handle* hc = nullptr;
+      if (create_handle(tv, n_vols, *tc, oc, lane, 128, st, &hc) != PRISM_OK) {
+        g_err.clear();
+        continue;
+      }
+      int rc = PRISM_OK;
+      for (int i = 0; i < 2 && rc == PRISM_OK; ++i) rc = enqueue_fused_iter(hc, st);
+      cudaEventRecord(e0, st);
+      for (int i = 0; i < 4 && rc == PRISM_OK; ++i) rc = enqueue_fused_iter(hc, st);
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      const bool shell_used = hc->shell;
+      delete hc;
+      if (rc == PRISM_OK && ms < best) {
+        best = ms;
+        *tpv = lane;
+        *shells = shell_used ? 0 : -1;
+      }
+      // the per-measurement loop is a second candidate only where the shell loop applied
+      if (!shell_used) break;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGetLastError();
+  g_err.clear();
 }
 
 }  // namespace
@@ -983,39 +1208,9 @@ extern "C" int prism_fit_init(const prism_volume* vols, int32_t n_vols, const pr
   int tpv = 1, nt = 128;
   choose_shape(o, V, &tpv, &nt);
   if (o.autotune && o.fused) {
-    // Time each candidate tile shape for a few iterations on the real data; keep the fastest.
-    const int cands[3][2] = {{1, 128}, {4, 128}, {16, 128}};
-    float best = 1e30f;
-    prism_options oc = o;
-    oc.use_graph = 0;
-    oc.autotune = 0;
-    cudaEvent_t e0, e1;
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
-    for (const auto& c : cands) {
-      if (o.threads_per_voxel && c[0] != o.threads_per_voxel) continue;
-      prism_handle* hc = nullptr;
-      if (create_handle(vols, n_vols, counts, oc, c[0], c[1], st, &hc) != PRISM_OK) {
-        g_err.clear();
-        continue;
-      }
-      int rc = enqueue_fused_iter(hc, st);
-      cudaEventRecord(e0, st);
-      for (int i = 0; i < 3 && rc == PRISM_OK; ++i) rc = enqueue_fused_iter(hc, st);
-      cudaEventRecord(e1, st);
-      cudaEventSynchronize(e1);
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      delete hc;
-      if (rc == PRISM_OK && ms < best) {
-        best = ms;
-        tpv = c[0];
-        nt = c[1];
-      }
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    g_err.clear();
+    int shells = o.shells;
+    autotune_shape(vols, n_vols, counts, o, st, &tpv, &shells);
+    o.shells = shells;
   }
   prism_handle* h = nullptr;
   const int rc = create_handle(vols, n_vols, counts, o, tpv, nt, st, &h);
@@ -1074,11 +1269,12 @@ extern "C" int prism_info(const prism_handle* h, int64_t* n_vox, int32_t* n_grou
 }
 
 extern "C" int prism_get_shape(const prism_handle* h, int32_t* threads_per_voxel, int32_t* tile_voxels,
-                               int32_t* fused_grid) {
+                               int32_t* fused_grid, int32_t* shell_loop) {
   if (!h) return fail(PRISM_E_INVALID_ARG, "handle is NULL");
   if (threads_per_voxel) *threads_per_voxel = h->TPV;
   if (tile_voxels) *tile_voxels = h->TV;
   if (fused_grid) *fused_grid = h->opt.fused ? h->fused_grid : 0;
+  if (shell_loop) *shell_loop = h->shell ? 1 : 0;
   return PRISM_OK;
 }
 
@@ -1259,10 +1455,11 @@ extern "C" int prism_profile(prism_handle* h, int32_t n_iters, void* stream, flo
   for (int i = 0; i < n_iters && rc == PRISM_OK; ++i) {
     cudaError_t e = cudaEventRecord(ev[0], st);
     if (e == cudaSuccess && h->opt.lam_sp > 0.f) e = h->ks->prior_prep(a, 0, h->ntiles, st);
-    if (e == cudaSuccess && h->nb && h->TPV > 1) e = h->ks->prior_grad(a, 0, h->ntiles, st);
+    if (e == cudaSuccess && h->nb) e = h->ks->prior_grad(a, 0, h->ntiles, st);
     if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
     if (e == cudaSuccess)
-      e = h->ks->fused(a, h->opt.loss, h->cal ? 1 : 0, h->TPV, h->fused_grid, h->NT, h->fused_smem, st);
+      e = h->ks->fused(a, h->opt.loss, h->cal ? 1 : 0, h->TPV, h->shell ? 1 : 0, h->fused_grid, h->NT, h->fused_smem,
+                       st);
     if (e == cudaSuccess) e = cudaEventRecord(ev[2], st);
     if (e == cudaSuccess && h->cal) e = launch_bias_grad(a, h->ga, st);
     if (e == cudaSuccess && h->cal) e = launch_group_reduce(a, h->ga, 1 | 2, st);
@@ -1379,16 +1576,6 @@ extern "C" int prism_set_state(prism_handle* h, const void* host_buf, int64_t by
 
 namespace {
 // Device buffer released on scope exit (temporaries of the slab entry points).
-struct DevTmp {
-  void* p = nullptr;
-  ~DevTmp() {
-    if (p) cudaFree(p);
-  }
-  template <typename T>
-  T* as() const {
-    return static_cast<T*>(p);
-  }
-};
 }  // namespace
 
 extern "C" int prism_fit_init_slabs(const prism_volume* vol, int32_t slab, int32_t overlap, const prism_options* opt,

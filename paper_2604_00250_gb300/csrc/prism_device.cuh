@@ -45,6 +45,21 @@ struct __align__(16) MeasPair {
 // Field positions (MeasRow order) of e^alpha_n and beta_n in the paired table.
 constexpr int kPairFieldA = 11, kPairFieldBeta = 12;
 
+// One run of equal b-values in a group's table order (a shell), for the shell loop of the fused
+// kernel (one thread per voxel, MSE, no calibration): measurement pairs [p0, p1), the isotropic
+// decays of Eq. 4 at this b, and the shell's constants of the scaled fiber terms (Eq. 5 with
+// c' = s c, s = sqrt(b D_par log2 e)):
+//   f_in e1 = 2^(log2 f_in - c'^2),   (1 - f_in) p = 2^(rho (log2 f_in - c'^2) + C0 - b D_perp log2 e)
+// with rho = 1 - D_perp / D_par and C0 = log2(1 - f_in) - rho log2 f_in per voxel, and
+//   dE_wm/dc = (c' / s) (A_n f_in e1 + B_n (1 - f_in) p),  ap = A_n / s, bp = B_n / s.
+struct __align__(16) ShellRun {
+  int32_t p0, p1, b0, pad;         // pairs [p0, p1); b0 = 1 for b = 0 (every E of Eqs. 4-5 is 1)
+  float ecsf, egm, eres, nbperp;   // E_csf, E_gm, E_res; -b D_perp log2(e)
+  float s, ap, bp, pad2;           // sqrt(b D_par log2 e); -2 b D_par / s; 2 b (D_perp - D_par) / s (0 at b = 0)
+};
+constexpr int kMaxRuns = 16;        // shells per group the shell loop takes
+constexpr float kRho = 1.f - 0.4f / 1.7f;   // 1 - D_perp / D_par (Eq. 5)
+
 // A tile: up to TV voxels of one patch, processed by one CTA.
 struct Tile {
   int32_t group, patch, slot0, count;
@@ -65,6 +80,10 @@ struct GroupDev {
   int64_t grid_off;    // offset of the group's [nx][ny][nz] slot map
   int32_t table2_off;  // first MeasPair of the group
   int32_t nb0p;        // leading table pairs whose two measurements both have b = 0 (see meas_order)
+  int32_t run_off;     // first ShellRun of the group (shell loop)
+  int32_t n_runs;      // its shells
+  int32_t gtab_off;    // float offset of the group's gradient table [3][NP] (g_x, g_y, g_z rows)
+  int32_t pad_;
 };
 
 // Kernel arguments shared by the iteration kernels (passed by value).
@@ -87,6 +106,8 @@ struct IterArgs {
   const uint32_t* vflag;   // [Vpad] bits 0-5 TV neighbours (+x,-x,+y,-y,+z,-z) masked; bits 8-12 |N(x)|
   const MeasRow* table;    // per-group measurement tables
   const MeasPair* table2;  // the same, paired (see MeasPair)
+  const float* gtab;       // per group [3][NP] gradient directions in table order (shell loop)
+  const ShellRun* runs;    // per group shells in table order (shell loop)
   const float* gparams;    // packed group parameters
   float* gU;               // [Vpad] dJ/dU(x)
   float* tile_ab;          // per-tile [2][N] alpha / beta gradient partials

@@ -78,8 +78,9 @@ __device__ __forceinline__ float fsqrt(float x) {
   return y;
 }
 
-// Gradient w.r.t. transformed parameters -> raw parameters (adjoint of `transform`).
-template <int K>
+// Gradient w.r.t. transformed parameters -> raw parameters (adjoint of `transform`). With
+// RAWU, gfin is already the derivative w.r.t. the raw u of f_intra = sigmoid(u).
+template <int K, bool RAWU = false>
 __device__ __forceinline__ void chain_raw(const Vox<K>& P, float gS0, const float (&gf)[K + 3],
                                           const float (&gd)[K][3], float gfin, float (&g)[4 * K + 5]) {
   constexpr int NF = K + 3;
@@ -95,7 +96,7 @@ __device__ __forceinline__ void chain_raw(const Vox<K>& P, float gS0, const floa
 #pragma unroll
     for (int c = 0; c < 3; ++c) g[K + 4 + 3 * k + c] = (gd[k][c] - pd * P.d[k][c]) * P.inrm[k];
   }
-  g[4 * K + 4] = gfin * P.fin * P.omf;
+  g[4 * K + 4] = RAWU ? gfin : gfin * P.fin * P.omf;
 }
 
 // Writes the fractions and unit directions a neighbour needs (xf layout [4K+3][Vpad]).
@@ -734,6 +735,193 @@ __device__ __forceinline__ void block_reduce3(double v0, double v1, double v2, d
   }
 }
 
+// ---------------------------------------------------------------------------
+// Shell loop (one thread per voxel, MSE, no calibration): the group's measurements are in
+// b-value order, so runs of equal b (shells, ShellRun) share Eq. 4's isotropic decays and Eq.
+// 5's exponent constants. Per shell and voxel the isotropic mixture T0 is formed once and the
+// isotropic adjoint sums need only sum_n r over the shell; per measurement and fiber the two
+// exponentials come from the scaled cosine c' = s c (see ShellRun):
+//   m = c'^2 - log2 f_in,  f_in e1 = 2^(-m),  (1 - f_in) p = 2^(-rho m + Kp),
+//   T = T0 + sum_k f_k (f_in e1 + (1 - f_in) p),  r = y - S0 T  (two measurements per step).
+// The adjoint sums are ga_k = sum r f_in e1, gb_k = sum r (1 - f_in) p and
+// gd_k = sum r c' (ap f_in e1 + bp (1 - f_in) p) g = sum r dE_wm,k/dc g.
+// Per-voxel scalars needed only at shell changes sit in a per-thread column of shared memory.
+// ---------------------------------------------------------------------------
+constexpr int kFusedThreadsShell = 128;   // threads of the fused kernel's CTA (kFusedThreads)
+
+template <int K>
+struct ShellState {
+  float2 f[K];          // fiber fractions f_wm,k (duplicated)
+  float2 dp[K][3];      // s d_k of the current shell
+  float2 nlfin;         // -log2 f_in
+  float2 nS0;           // -S0
+  float2 T0;            // isotropic mixture of the shell (b = 0: the sum of all fractions)
+  float2 Kp;            // C0 - b D_perp log2(e)
+  float2 ap, bp;        // the shell's ap, bp
+  float2 l1, Qs;        // sum r^2; sum r over the current shell
+  float2 ga[K], gb[K];
+  float2 gd[K][3];
+  int ri, pend, b0;     // current shell, its end pair, b = 0 flag
+};
+
+// Rows of a thread's shared-memory column (stride kFusedThreads): d_k (3K), f_csf, f_gm,
+// f_res, f_in, 1 - f_in, C0, then the sums sum_n r E_csf, sum_n r E_gm, sum_n r E_res.
+template <int K>
+struct ShellRows {
+  static constexpr int dir = 0, fcsf = 3 * K, fgm = 3 * K + 1, fres = 3 * K + 2, fin = 3 * K + 3, omf = 3 * K + 4,
+                       c0 = 3 * K + 5, gcsf = 3 * K + 6, ggm = 3 * K + 7, gres = 3 * K + 8, count = 3 * K + 9;
+};
+
+template <int K>
+__device__ __forceinline__ void shell_step(ShellState<K>& S, float2 gx, float2 gy, float2 gz, float2 y) {
+  const float2 nrho = make_float2(-kRho, -kRho);
+  float2 cp[K], e1[K], pp[K], t[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    cp[k] = __ffma2_rn(S.dp[k][0], gx, __ffma2_rn(S.dp[k][1], gy, __fmul2_rn(S.dp[k][2], gz)));
+    const float2 m = __ffma2_rn(cp[k], cp[k], S.nlfin);
+    e1[k] = make_float2(ex2f_(-m.x), ex2f_(-m.y));
+    pp[k] = ex2_2(__ffma2_rn(nrho, m, S.Kp));
+    t[k] = __fadd2_rn(e1[k], pp[k]);
+  }
+  float2 T = __ffma2_rn(S.f[0], t[0], S.T0);
+#pragma unroll
+  for (int k = 1; k < K; ++k) T = __ffma2_rn(S.f[k], t[k], T);
+  const float2 r = __ffma2_rn(S.nS0, T, y);   // y - y_hat
+  S.l1 = __ffma2_rn(r, r, S.l1);
+  S.Qs = __fadd2_rn(S.Qs, r);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    S.ga[k] = __ffma2_rn(r, e1[k], S.ga[k]);
+    S.gb[k] = __ffma2_rn(r, pp[k], S.gb[k]);
+    const float2 inner = __ffma2_rn(S.bp, pp[k], __fmul2_rn(S.ap, e1[k]));
+    const float2 w = __fmul2_rn(__fmul2_rn(r, cp[k]), inner);
+    S.gd[k][0] = __ffma2_rn(w, gx, S.gd[k][0]);
+    S.gd[k][1] = __ffma2_rn(w, gy, S.gd[k][1]);
+    S.gd[k][2] = __ffma2_rn(w, gz, S.gd[k][2]);
+  }
+}
+
+// Closes the current shell: its sum_n r goes into the isotropic sums (and, at b = 0, where
+// f_in e1 = f_in and (1 - f_in) p = 1 - f_in, into ga / gb).
+template <int K>
+__device__ __forceinline__ void shell_close(ShellState<K>& S, const ShellRun& R, float* col) {
+  using SR = ShellRows<K>;
+  const float q = S.Qs.x + S.Qs.y;
+  col[SR::gcsf * kFusedThreadsShell] = fmaf(R.ecsf, q, col[SR::gcsf * kFusedThreadsShell]);
+  col[SR::ggm * kFusedThreadsShell] = fmaf(R.egm, q, col[SR::ggm * kFusedThreadsShell]);
+  col[SR::gres * kFusedThreadsShell] = fmaf(R.eres, q, col[SR::gres * kFusedThreadsShell]);
+  if (R.b0) {
+    const float2 fi = dup2(col[SR::fin * kFusedThreadsShell]), om = dup2(col[SR::omf * kFusedThreadsShell]);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      S.ga[k] = __ffma2_rn(fi, S.Qs, S.ga[k]);
+      S.gb[k] = __ffma2_rn(om, S.Qs, S.gb[k]);
+    }
+  }
+  S.Qs = make_float2(0.f, 0.f);
+}
+
+// Opens shell R: its isotropic mixture, exponent offset, derivative constants and s d_k.
+template <int K>
+__device__ __forceinline__ void shell_open(ShellState<K>& S, const ShellRun& R, const float* col) {
+  using SR = ShellRows<K>;
+  constexpr int C = kFusedThreadsShell;
+  S.pend = R.p1;
+  S.b0 = R.b0;
+  float T0 = fmaf(col[SR::fcsf * C], R.ecsf, fmaf(col[SR::fgm * C], R.egm, col[SR::fres * C] * R.eres));
+  if (R.b0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) T0 += S.f[k].x;
+  }
+  S.T0 = dup2(T0);
+  S.Kp = dup2(col[SR::c0 * C] + R.nbperp);
+  S.ap = dup2(R.ap);
+  S.bp = dup2(R.bp);
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) S.dp[k][c] = dup2(R.s * col[(SR::dir + 3 * k + c) * C]);
+}
+
+// Voxel set-up of the shell loop from the transformed parameters (its column and registers).
+template <int K>
+__device__ __forceinline__ void shell_begin(ShellState<K>& S, const Vox<K>& P, float* col) {
+  using SR = ShellRows<K>;
+  constexpr int C = kFusedThreadsShell;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    S.f[k] = dup2(P.f[2 + k]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) col[(SR::dir + 3 * k + c) * C] = P.d[k][c];
+  }
+  // log2 f_in and log2(1 - f_in), floored so that a saturated f_in gives no inf - inf
+  const float lfin = fmaxf(lg2f_(P.fin), -40.f), lomf = fmaxf(lg2f_(P.omf), -126.f);
+  S.nlfin = dup2(-lfin);
+  S.nS0 = dup2(-P.S0);
+  col[SR::fcsf * C] = P.f[0];
+  col[SR::fgm * C] = P.f[1];
+  col[SR::fres * C] = P.f[K + 2];
+  col[SR::fin * C] = P.fin;
+  col[SR::omf * C] = P.omf;
+  col[SR::c0 * C] = fmaf(-kRho, lfin, lomf);
+  col[SR::gcsf * C] = col[SR::ggm * C] = col[SR::gres * C] = 0.f;
+  const float2 z = make_float2(0.f, 0.f);
+  S.l1 = S.Qs = z;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    S.ga[k] = S.gb[k] = z;
+    S.gd[k][0] = S.gd[k][1] = S.gd[k][2] = z;
+  }
+  S.ri = -1;
+  S.pend = 0;
+  S.b0 = 0;
+}
+
+// The shell loop's sums as the (unscaled, q = y_hat - y) accumulators of the epilogue:
+// gwa_k = sum q f_in e1, gwb_k = sum q (1 - f_in) p (the scaled forms), gS0 = sum q T.
+template <int K>
+__device__ __forceinline__ void shell_fold(const Vox<K>& P, const ShellState<K>& S, const float* col, Acc<K>& A) {
+  using SR = ShellRows<K>;
+  constexpr int C = kFusedThreadsShell;
+  A.gcsf = -col[SR::gcsf * C];
+  A.ggm = -col[SR::ggm * C];
+  A.gres = -col[SR::gres * C];
+  A.l1 = S.l1.x + S.l1.y;
+  float g = P.f[0] * A.gcsf + P.f[1] * A.ggm + P.f[K + 2] * A.gres;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    A.gwa[k] = -(S.ga[k].x + S.ga[k].y);
+    A.gwb[k] = -(S.gb[k].x + S.gb[k].y);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) A.gd[k][c] = -(S.gd[k][c].x + S.gd[k][c].y);
+    g = fmaf(P.f[2 + k], A.gwa[k] + A.gwb[k], g);
+  }
+  A.gS0 = g;
+}
+
+// Scaled data-term gradient from the shell loop's sums; gu is w.r.t. the raw u of f_in:
+// dE_wm/du = f_in (1 - f_in) (e1 - p) = (1 - f_in) (f_in e1) - f_in ((1 - f_in) p).
+template <int K>
+__device__ __forceinline__ void data_grad_shell(const Vox<K>& P, const Acc<K>& A, float scale, float& gS0,
+                                                float (&gf)[K + 3], float (&gd)[K][3], float& gu) {
+  const float sS = scale * P.S0;
+  gS0 = A.gS0 * scale;
+  gf[0] = A.gcsf * sS;
+  gf[1] = A.ggm * sS;
+  gf[K + 2] = A.gres * sS;
+  float gin = 0.f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    gf[2 + k] = (A.gwa[k] + A.gwb[k]) * sS;
+    gin = fmaf(P.f[2 + k], fmaf(P.omf, A.gwa[k], -P.fin * A.gwb[k]), gin);
+    const float w = sS * P.f[2 + k];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) gd[k][c] = A.gd[k][c] * w;
+  }
+  gu = gin * sS;
+}
+
 // ===========================================================================
 // Fused iteration: one persistent kernel over the tile queue does synthesis,
 // calibration, data term, adjoint, priors, chain rule and the voxel Adam update.
@@ -749,6 +937,7 @@ constexpr int kChunk = 32;    // measurements per ring stage
 constexpr int kCalG = 4;      // measurements per warp reduce-scatter of the calibration partials
 constexpr int kStages = 2;    // ring depth per warp
 constexpr int kFusedThreads = 128;
+static_assert(kFusedThreads == kFusedThreadsShell, "the shell loop's shared-memory columns use the CTA size");
 
 // Adam / Rprop state of one voxel. Every load is issued before any store of the update (the
 // stores could alias the loads as far as the compiler knows, which would serialise one memory
@@ -844,13 +1033,17 @@ constexpr int fused_min_blocks() {
   return ((K >= 5) || (fused_packed<K, TPV, LOSS, CAL>() && (CAL || LOSS == kLossNLL))) ? 3 : 4;
 }
 
-template <int K, int TPV, int LOSS, bool CAL>
+// SHELL: the shell loop (see ShellState) instead of the packed pairs; only for one thread per
+// voxel, the MSE, no calibration and K <= 3, with every group's shells of even length.
+template <int K, int TPV, int LOSS, bool CAL, bool SHELL = false>
 __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<K, TPV, LOSS, CAL>())) k_iter_fused(const IterArgs a) {
   constexpr int NF = K + 3, Q = 4 * K + 5, XF = 4 * K + 3;
   constexpr int NW = kFusedThreads / 32;
   constexpr int VW = 32 / TPV;              // voxels per warp
   constexpr bool PACKED = fused_packed<K, TPV, LOSS, CAL>();
   constexpr bool HOIST = PACKED && TPV == 1 && K <= 3 && LOSS == kLossMSE && !CAL;
+  static_assert(!SHELL || HOIST, "the shell loop covers one thread per voxel, MSE, no calibration, K <= 3");
+  using SR = ShellRows<(K <= 3 ? K : 3)>;
   // ring stages per warp (kStages; a ring as deep in bytes for four or sixteen lanes per voxel,
   // kStages * TPV, measured 0-25 % slower)
   constexpr int NS = kStages;
@@ -858,7 +1051,12 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<K, TPV, LOSS,
   extern __shared__ __align__(16) unsigned char smem[];
   const int Vp = a.Vpad;
   MeasRow* s_tab = reinterpret_cast<MeasRow*>(smem);
-  float* s_ring = reinterpret_cast<float*>(s_tab + a.Nmax);                 // [NW][NS][kChunk][VW]
+  // shell loop: [3][Nmax] gradient rows, kMaxRuns shells, the threads' columns, then the ring
+  float* s_g = reinterpret_cast<float*>(smem);
+  ShellRun* s_runs = reinterpret_cast<ShellRun*>(s_g + 3 * a.Nmax);
+  float* s_col = reinterpret_cast<float*>(s_runs + kMaxRuns);
+  float* s_ring = SHELL ? s_col + SR::count * kFusedThreads
+                        : reinterpret_cast<float*>(s_tab + a.Nmax);       // [NW][NS][kChunk][VW]
   float* s_blr = s_ring + NW * NS * kChunk * VW;                       // [512] (calibration)
   float* s_ab = s_blr + (CAL ? kNGrid : 0);                                 // [NW][2][Nmax] (calibration)
   __shared__ uint64_t s_bar;                 // table / bias grid
@@ -930,7 +1128,13 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<K, TPV, LOSS,
     if (tl.group != cur_group) {
       if (tid == 0) {
         fence_proxy_async_smem();
-        if (PACKED) {
+        if (SHELL) {
+          const uint32_t gb = 3u * static_cast<uint32_t>(NP) * 4u;
+          const uint32_t rb = static_cast<uint32_t>(gr.n_runs) * static_cast<uint32_t>(sizeof(ShellRun));
+          mbar_expect_tx(&s_bar, gb + rb);
+          tma_bulk_g2s(s_g, a.gtab + gr.gtab_off, gb, &s_bar);
+          tma_bulk_g2s(s_runs, a.runs + gr.run_off, rb, &s_bar);
+        } else if (PACKED) {
           const uint32_t tb = static_cast<uint32_t>(NP / 2 * sizeof(MeasPair));
           mbar_expect_tx(&s_bar, tb + (CAL ? kNGrid * 4u : 0u));
           tma_bulk_g2s(s_tab, a.table2 + gr.table2_off, tb, &s_bar);
@@ -960,7 +1164,7 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<K, TPV, LOSS,
           prefetch_l2(a.m + o, rb);
           prefetch_l2(a.v + o, rb);
         }
-        if (a.nb_priors && TPV > 1) {
+        if (a.nb_priors) {
           for (int c = 0; c < kPgRows<K>; ++c) prefetch_l2(a.pg + static_cast<size_t>(c) * Vp + slot0, rb);
         } else if (a.nb_priors) {
           for (int e = 0; e < a.n_nbr; ++e) prefetch_l2(a.nbr + static_cast<size_t>(e) * Vp + slot0, rb);
@@ -998,7 +1202,13 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<K, TPV, LOSS,
     fiber_weights<K>(P, ffin, fomf);
     VoxP<K> DP;
     AccP<K> AP;
-    if constexpr (PACKED) voxp_init<K>(P, DP, AP);
+    ShellState<(K <= 3 ? K : 3)> SS;
+    float* col = s_col + tid;
+    if constexpr (SHELL) {
+      shell_begin(SS, P, col);
+    } else if constexpr (PACKED) {
+      voxp_init<K>(P, DP, AP);
+    }
     for (int j = 0; j < nch; ++j) {
       if (lane == 0) {
         // keep NS chunks of this warp's stream in flight (this tile, then the next)
@@ -1016,6 +1226,44 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<K, TPV, LOSS,
         failed = true;
       }
       const int cnt = min(kChunk, N - j * kChunk);
+      if constexpr (SHELL) {
+        // pairs of this chunk, in segments that stay inside one shell (shells have even lengths)
+        const float2* __restrict__ yc2 = reinterpret_cast<const float2*>(ring + s * (kChunk * VW)) + lv;
+        const float2* __restrict__ gx2 = reinterpret_cast<const float2*>(s_g);
+        const float2* __restrict__ gy2 = reinterpret_cast<const float2*>(s_g + NP);
+        const float2* __restrict__ gz2 = reinterpret_cast<const float2*>(s_g + 2 * NP);
+        const int pc0 = j * (kChunk / 2), pc1 = min(pc0 + kChunk / 2, N / 2);
+        if (act) {
+          int p = pc0;
+          while (p < pc1) {
+            if (p >= SS.pend) {
+              // every pass either opens a shell (at most n_runs) or advances p, so this ends
+              // even for a table that did not cover the pairs
+              if (SS.ri + 1 >= gr.n_runs) break;
+              if (SS.ri >= 0) shell_close(SS, s_runs[SS.ri], col);
+              ++SS.ri;
+              shell_open(SS, s_runs[SS.ri], col);
+              continue;
+            }
+            const int pe = min(pc1, SS.pend);
+            if (SS.b0) {
+#pragma unroll 1
+              for (; p < pe; ++p) {
+                const float2 r = __ffma2_rn(SS.nS0, SS.T0, yc2[(p - pc0) * VW]);
+                SS.l1 = __ffma2_rn(r, r, SS.l1);
+                SS.Qs = __fadd2_rn(SS.Qs, r);
+              }
+            } else {
+              // four steps in flight (2 % faster than two on the brain workload; no spills)
+#pragma unroll 4
+              for (; p < pe; ++p) shell_step(SS, gx2[p], gy2[p], gz2[p], yc2[(p - pc0) * VW]);
+            }
+          }
+        }
+        __syncwarp();
+        ++g;
+        continue;
+      }
       if constexpr (PACKED) {
         const float2* __restrict__ yc2 = reinterpret_cast<const float2*>(ring + s * (kChunk * VW)) + lv;
         const MeasPair* __restrict__ tab2 = reinterpret_cast<const MeasPair*>(s_tab) + j * (kChunk / 2);
@@ -1162,6 +1410,9 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<K, TPV, LOSS,
       ++g;
     }
     base += nch;
+    if constexpr (SHELL) {
+      if (act && SS.ri >= 0) shell_close(SS, s_runs[SS.ri], col);
+    }
     if constexpr (TPV > 1) {
       // sum each voxel's lanes and hand the sums to one epilogue thread: voxel v of the tile
       // goes to thread v, so that a warp's epilogue serves 32 voxels, as with one thread per voxel
@@ -1186,7 +1437,11 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<K, TPV, LOSS,
       if constexpr (HOIST) load_moments<Q>(a, eslot, writer, mq, vq);
       transform<K>(th, P);
       if constexpr (TPV == 1) {
-        if constexpr (PACKED) accp_fold<K, LOSS, CAL>(P, AP, A);
+        if constexpr (SHELL) {
+          shell_fold(P, SS, col, A);
+        } else if constexpr (PACKED) {
+          accp_fold<K, LOSS, CAL>(P, AP, A);
+        }
       } else {
         acc_get<K>(A, s_acc, TV, tid);
         if constexpr (PACKED) A.gS0 = acc_gS0<K>(P, A);
@@ -1198,7 +1453,11 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<K, TPV, LOSS,
 
       // ---- data-term gradient and value
       float gS0, gf[NF], gd[K][3], gfin;
-      data_grad<K>(P, A, scale, gS0, gf, gd, gfin);
+      if constexpr (SHELL) {
+        data_grad_shell<K>(P, A, scale, gS0, gf, gd, gfin);   // gfin: w.r.t. the raw u
+      } else {
+        data_grad<K>(P, A, scale, gS0, gf, gd, gfin);
+      }
       if (LOSS == kLossMSE) {
         dloss = A.l1 * gr.inv_M;
       } else {
@@ -1206,7 +1465,7 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<K, TPV, LOSS,
         dsig = 2.f * N - inv_s2 * (A.l1 + 2.f * A.l2);
       }
       // ---- priors
-      ploss = priors<K, (TPV > 1)>(a, P, eslot, gr.inv_M, xf_cur, gS0, gf, gd);
+      ploss = priors<K, true>(a, P, eslot, gr.inv_M, xf_cur, gS0, gf, gd);
       float gUv = A.u * scale;
       if (CAL && a.w_tv > 0.f) {
         const uint32_t fl = eact ? a.vflag[eslot] : 0u;
@@ -1218,7 +1477,7 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<K, TPV, LOSS,
         load_moments<Q>(a, eslot, writer, mq, vq);
       }
       float gq[Q];
-      chain_raw<K>(P, gS0, gf, gd, gfin, gq);
+      chain_raw<K, SHELL>(P, gS0, gf, gd, gfin, gq);
       if (a.optimizer == 0) {
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
@@ -1644,11 +1903,11 @@ __global__ void k_prior_prep(const IterArgs a, int tile_begin, int tile_end) {
   a.lp[slot] = a.lam_sp * gr.inv_M * val;
 }
 
-// Neighbour priors of every voxel for the fused kernel with several lanes per voxel (after
-// k_prior_prep, from the current fractions and directions): the kPgRows<K> rows that its
-// epilogue then reads with one coalesced load each instead of gathering the neighbourhood
-// there. (With one thread per voxel the gathers stay in the epilogue: moving them here
-// took 40 us of 0.60 ms and saved 39 us of the fused kernel on the brain workload.)
+// Neighbour priors of every voxel for the fused kernel (after k_prior_prep, from the current
+// fractions and directions): the kPgRows<K> rows that its epilogue then reads with one
+// coalesced load each instead of gathering the neighbourhood there, where the gathers'
+// latency stalls the tile (on the brain workload with one thread per voxel: about 30 us here
+// against 68 us of the fused kernel's epilogue).
 template <int K>
 __global__ void k_prior_grad(const IterArgs a, int tile_begin, int tile_end) {
   constexpr int NF = K + 3, XF = 4 * K + 3;

@@ -12,18 +12,18 @@ namespace {
 
 constexpr int kK = PRISM_K;
 
-template <int TPV, int LOSS, bool CAL>
+template <int TPV, int LOSS, bool CAL, bool SHELL = false>
 cudaError_t fused_one(const IterArgs& a, int grid, int nt, size_t smem, cudaStream_t st) {
-  auto fn = k_iter_fused<kK, TPV, LOSS, CAL>;
+  auto fn = k_iter_fused<kK, TPV, LOSS, CAL, SHELL>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   fn<<<grid, nt, smem, st>>>(a);
   return cudaGetLastError();
 }
 
-template <int TPV, int LOSS, bool CAL>
+template <int TPV, int LOSS, bool CAL, bool SHELL = false>
 cudaError_t fused_occ(int nt, size_t smem, int* blocks) {
-  auto fn = k_iter_fused<kK, TPV, LOSS, CAL>;
+  auto fn = k_iter_fused<kK, TPV, LOSS, CAL, SHELL>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fn, nt, smem);
@@ -47,7 +47,14 @@ cudaError_t occ_tpv(int loss, int cal, int nt, size_t smem, int* blocks) {
   return cal ? fused_occ<TPV, kLossNLL, true>(nt, smem, blocks) : fused_occ<TPV, kLossNLL, false>(nt, smem, blocks);
 }
 
-cudaError_t l_fused(const IterArgs& a, int loss, int cal, int tpv, int grid, int nt, size_t smem, cudaStream_t st) {
+cudaError_t l_fused(const IterArgs& a, int loss, int cal, int tpv, int shell, int grid, int nt, size_t smem,
+                    cudaStream_t st) {
+  if constexpr (kK <= 3) {
+    if (shell) {
+      if (tpv != 1 || loss != kLossMSE || cal) return cudaErrorInvalidValue;
+      return fused_one<1, kLossMSE, false, true>(a, grid, nt, smem, st);
+    }
+  }
   switch (tpv) {
     case 1: return fused_tpv<1>(a, loss, cal, grid, nt, smem, st);
     case 4: return fused_tpv<4>(a, loss, cal, grid, nt, smem, st);
@@ -56,7 +63,13 @@ cudaError_t l_fused(const IterArgs& a, int loss, int cal, int tpv, int grid, int
   }
 }
 
-cudaError_t l_fused_occupancy(int loss, int cal, int tpv, int nt, size_t smem, int* blocks) {
+cudaError_t l_fused_occupancy(int loss, int cal, int tpv, int shell, int nt, size_t smem, int* blocks) {
+  if constexpr (kK <= 3) {
+    if (shell) {
+      if (tpv != 1 || loss != kLossMSE || cal) return cudaErrorInvalidValue;
+      return fused_occ<1, kLossMSE, false, true>(nt, smem, blocks);
+    }
+  }
   switch (tpv) {
     case 1: return occ_tpv<1>(loss, cal, nt, smem, blocks);
     case 4: return occ_tpv<4>(loss, cal, nt, smem, blocks);

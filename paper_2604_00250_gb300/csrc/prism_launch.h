@@ -9,9 +9,10 @@ namespace prism {
 
 // Per-K launchers of the templated kernels (one translation unit per K).
 struct KernelSet {
-  cudaError_t (*fused)(const IterArgs& a, int loss, int cal, int tpv, int grid, int nt, size_t smem,
+  // shell = 1: the shell loop of one thread per voxel, MSE, no calibration (K <= 3)
+  cudaError_t (*fused)(const IterArgs& a, int loss, int cal, int tpv, int shell, int grid, int nt, size_t smem,
                        cudaStream_t st);
-  cudaError_t (*fused_occupancy)(int loss, int cal, int tpv, int nt, size_t smem, int* blocks);
+  cudaError_t (*fused_occupancy)(int loss, int cal, int tpv, int shell, int nt, size_t smem, int* blocks);
   cudaError_t (*transform)(const IterArgs& a, int tb, int te, cudaStream_t st);
   cudaError_t (*synth)(const IterArgs& a, const PlainArgs& p, int cal, int tpv, int nt, cudaStream_t st);
   cudaError_t (*adjoint)(const IterArgs& a, const PlainArgs& p, int cal, int tpv, int nt, size_t smem,

@@ -155,7 +155,7 @@ def test_readout_entry_points_reject_null_handles(prism):
     lib = prism._lib.load()
     assert lib.prism_get_fibers(None, None, None, None, ctypes.c_float(0.15), 0, None) == 1
     assert lib.prism_stitch_slabs(None, None, None, None, None, 0, None) == 1
-    assert lib.prism_get_shape(None, None, None, None) == 1
+    assert lib.prism_get_shape(None, None, None, None, None) == 1
 
 
 def test_host_plan_runs_on_a_machine_without_a_gpu(prism):

@@ -133,6 +133,7 @@ def test_brain_bench_configuration_fused_gradient():
                               bvecs=vol.bvecs, init=None)
     f = prism.Fitter([v], prism.options(fused=1, use_graph=1, **kw))
     assert f.shape()["threads_per_voxel"] == 1 and f.shape()["tile_voxels"] == 128
+    assert f.shape()["shell_loop"] == 1
     th0 = f.params_host()
     f.step(1)
     f.sync()

@@ -158,6 +158,7 @@ def test_brain_bench_configuration_sampled_patches():
                               bvecs=vol.bvecs, init=None)
     f = prism.Fitter([v], prism.options(fused=1, use_graph=1, **kw))
     assert f.shape()["threads_per_voxel"] == 1 and f.shape()["tile_voxels"] == 128
+    assert f.shape()["shell_loop"] == 1            # 18 b = 0 + 3 x 90: every shell even
     th0 = f.params_host()
     f.step(2)
     f.sync()
