@@ -60,6 +60,96 @@ FUSED_SOURCES = ("prism_kernels.cuh", "prism_device.cuh", "prism_kset.cuh", "bes
 FP32_LANES_PER_SM = 128
 
 
+def flops_per_measurement(loss, cal, K, shell):
+    """FP32 flops (fused multiply-add = 2) per (voxel, measurement) pair of the fused kernel's
+    loop, counted from its algorithm. Per-measurement loop, MSE: the 17 + 28 K above. With
+    calibration add 11: e^alpha_n B, S0 T, y_hat = . S + beta_n (4), the masked residual (3),
+    q = r e^alpha B, q S and its running sum (3), the alpha / beta partials' reduce-scatter (1
+    per value and measurement on average, 6 adds per 4 measurements and value) -- 28 + 28 K.
+    Rician NLL (Eq. 9), without calibration: the MSE's residual and square (4) give way to
+    y_hat = S0 T (1) and the NLL terms (71: z = y |y_hat| / sigma^2 2; Q(z) and L(z) from the
+    fitted functions of 4/z, 55 -- two degree-12 Horner chains 48, the argument and scale 3,
+    log terms 4; (y - |y_hat|)^2, y |y_hat| Q and L sums 9; dL/dy_hat 4; the rest 1) -- 85 + 28 K;
+    with calibration 94 + 28 K. Shell loop: 5 + 27 K (see FLOPS_PER_PAIR_SHELL)."""
+    if shell:
+        return 5 + 27 * K
+    if loss == "mse":
+        return (28 + 28 * K) if cal else (17 + 28 * K)
+    return (94 + 28 * K) if cal else (85 + 28 * K)
+
+
+def flops_per_voxel_iteration(bvals, loss, cal, K, shell):
+    """Per voxel of one volume: b = 0 measurements cost FLOPS_PER_B0_PAIR where the loop takes
+    them apart (MSE without calibration: the shell loop's b = 0 shell, or the leading b = 0
+    pairs of the per-measurement loop); every other measurement the loop's full cost."""
+    bv = np.asarray(bvals)
+    n0 = int(np.count_nonzero(bv == 0))
+    if loss == "mse" and not cal:
+        nb0 = n0 if shell else 2 * (n0 // 2)
+    else:
+        nb0 = 0
+    return (len(bv) - nb0) * flops_per_measurement(loss, cal, K, shell) + nb0 * FLOPS_PER_B0_PAIR
+
+
+def fp32_peak_tflops(device_index=0):
+    """SMs x 128 FP32 lanes x 2 flops x the maximum SM clock nvidia-smi reports (2070 MHz if
+    it reports none)."""
+    import torch
+    n_sm = torch.cuda.get_device_properties(device_index).multi_processor_count
+    mhz = 2070.0
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(device_index), "--query-gpu=clocks.max.sm",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=20).stdout
+        mhz = float(out.strip().splitlines()[0])
+    except (OSError, ValueError, IndexError, subprocess.SubprocessError):
+        pass
+    return n_sm * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12, f"{n_sm} SMs x {FP32_LANES_PER_SM} x 2 x {mhz:.0f} MHz"
+
+
+def speed_leg(vols, kw, steps, warmup, unfused_steps=2):
+    """Fused iterations (graph replay, CUDA events), the fused kernel's roofline fraction from the
+    per-kernel timing pass, and the plain per-patch path on the same volumes. `vols` hold device
+    signals."""
+    import torch
+    import paper_2604_00250_gb300 as prism
+    f = prism.Fitter(vols, prism.options(**kw))
+    f.step(warmup)
+    f.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    f.step(steps)
+    e1.record()
+    f.sync()
+    ms = e0.elapsed_time(e1) / steps
+    prof = f.profile(20)
+    shape = f.shape()
+    K = int(kw.get("K", 3))
+    loss, cal = kw.get("loss", "mse"), bool(kw.get("calibration", False))
+    flops = sum(int(np.count_nonzero(v.mask)) * flops_per_voxel_iteration(v.bvals, loss, cal, K, shape["shell_loop"])
+                for v in vols)
+    peak, peak_src = fp32_peak_tflops()
+    achieved = flops / (prof["fused_ms"] / 1e3) / 1e12
+    V = f.n_vox
+    f.close()
+    out = {"value": V / (ms / 1e3), "ms_per_step": ms, "steps": steps, "profile_ms": prof, "launch": shape,
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                        "kernel": "k_iter_fused", "flops_per_launch": flops, "peak_source": "derived: " + peak_src}}
+    if unfused_steps:
+        fu = prism.Fitter(vols, prism.options(**dict(kw, fused=0, use_graph=0)))
+        fu.step(1)
+        fu.sync()
+        u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        u0.record()
+        fu.step(unfused_steps)
+        u1.record()
+        fu.sync()
+        ms_u = u0.elapsed_time(u1) / unfused_steps
+        fu.close()
+        out["unfused"] = {"value": V / (ms_u / 1e3), "ms_per_step": ms_u, "steps": unfused_steps}
+        out["speedup_vs_unfused"] = ms_u / ms
+    return out
+
+
 def fused_sources_sha256():
     import hashlib
     h = hashlib.sha256()
@@ -171,6 +261,70 @@ def oracle_rate(vol, n_patches, iters, warm=1):
         times.append(time.perf_counter() - t0)
     dt = sum(times[warm:])
     return nvox * iters / dt, nvox, dt, torch.get_num_threads()
+
+
+def oracle_leg(vols, kw, iters=3, max_voxels=20000):
+    """The oracle as it stands on the host's cores: voxel-iterations/s of value_and_grad + Adam on
+    a bounded sample -- the volumes in order, each whole or (above max_voxels) its fullest 16^3
+    patches with the volume's |M|, until max_voxels."""
+    import torch
+    import phantoms as P
+    from oracle import prism_oracle as O
+    o = O.Options(**{k: v for k, v in kw.items() if hasattr(O.Options, k)})
+    left, nvox, dt = max_voxels, 0, 0.0
+    for v in vols:
+        if left <= 0:
+            break
+        patches = None
+        if v.n_vox > left:
+            m = np.asarray(v.mask).astype(bool)
+            coords = np.argwhere(m)
+            pshape = tuple(-(-s // o.patch_dim) for s in m.shape)
+            ids, counts = np.unique(np.ravel_multi_index(tuple((coords // o.patch_dim).T), pshape), return_counts=True)
+            order = np.argsort(-counts, kind="stable")
+            keep = np.cumsum(counts[order]) <= left
+            keep[0] = True
+            patches = ids[order][keep]
+        sig = v.signal.cpu().numpy() if hasattr(v.signal, "cpu") else np.asarray(v.signal)
+        ov = O.OracleVolume(v.mask, sig, v.bvals, v.bvecs, o, patches=patches)
+        th = torch.as_tensor(P.default_init(ov.n_vox, o.K, 0)).double()
+        gp = O.group_init(ov)
+        adam = O.Adam(o)
+        t0 = time.perf_counter()
+        for _ in range(iters):
+            adam.t += 1
+            _, _, g, gg = O.value_and_grad(ov, th, gp, n_norm=ov.n_mask)
+            th = adam.step("theta", th, g)
+            for name, gk in gg.items():
+                gp[name] = adam.step((name, 0), gp[name], gk)
+        dt += time.perf_counter() - t0
+        nvox += ov.n_vox
+        left -= ov.n_vox
+    return {"value": nvox * iters / dt, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"{nvox} voxels x {iters} iterations, {dt:.1f} s"}
+
+
+def run_small(args):
+    """The crossing patch (8^3, N = 96, MSE, K = 3; 'patch') and the crossing sweep (16 volumes
+    of 10^3 at 20-90 deg, N = 96, K = 3, MSE and the Rician NLL with sigma per volume; 'sweep'):
+    fused and unfused speed, the fused kernel's roofline fraction and the oracle on the host."""
+    import torch
+    import phantoms as P
+    if args.workload == "patch":
+        cases = [("crossing_patch_8cubed_N96_K3_mse", [P.crossing_patch(args.seed)], dict(K=3, loss="mse", patch_dim=8))]
+    else:
+        vols = P.crossing_sweep(args.seed)
+        cases = [(f"crossing_sweep_16x10cubed_N96_K3_{l}", vols, dict(K=3, loss=l, patch_dim=10)) for l in ("mse", "nll")]
+    import types
+    for name, vols, kw in cases:
+        gv = [types.SimpleNamespace(mask=v.mask, signal=torch.as_tensor(v.signal, device="cuda"), bvals=v.bvals,
+                                    bvecs=v.bvecs, init=None) for v in vols]
+        leg = speed_leg(gv, kw, min(args.steps, 500), args.warmup, unfused_steps=0 if args.no_unfused else 5)
+        line = {"workload": name, "voxels": int(sum(v.n_vox for v in vols)), "unit": UNIT, **leg, "options": kw}
+        if not args.no_cpu:
+            line["cpu_baseline"] = oracle_leg(vols, kw)
+        print(json.dumps(line), flush=True)
+    return 0
 
 
 def run_reference(args):
@@ -418,24 +572,17 @@ def run_calibrated(args):
     f = prism.Fitter(gv, prism.options(**opts))
     torch.cuda.synchronize()
     held = free0 - torch.cuda.mem_get_info()[0]
-    f.step(args.warmup)
-    f.sync()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    steps = min(args.steps, 500)
-    e0.record()
-    f.step(steps)
-    e1.record()
-    f.sync()
-    ms = e0.elapsed_time(e1) / steps
-    prof = f.profile(20)
+    n_vox, n_groups = f.n_vox, f.n_groups
+    f.close()
+    leg = speed_leg(gv, opts, min(args.steps, 500), args.warmup, unfused_steps=0 if args.no_unfused else 2)
     line = {"workload": ("bundle_64cubed_N360_nll_calibrated" if args.workload == "bundle"
                          else "multi_volume_12_edges_32_to_128_N96_288_360_nll_calibrated"),
-            "voxels": f.n_vox, "volumes": f.n_groups, "value": f.n_vox / (ms / 1e3),
-            "unit": "voxel-iterations/s", "ms_per_step": ms, "steps": steps, "profile_ms": prof,
+            "voxels": n_vox, "volumes": n_groups, "unit": "voxel-iterations/s", **leg,
             "signal_bytes": int(sum(v.signal.numel() * 4 for v in gv)), "fit_device_bytes": int(held),
             "options": opts}
+    if not args.no_cpu:
+        line["cpu_baseline"] = oracle_leg(vols, opts)
     print(json.dumps(line), flush=True)
-    f.close()
     return 0
 
 
@@ -466,10 +613,40 @@ def run_slabs(args):
         n_slab_vox, n_slabs = f.n_vox, f.n_groups
         f.close()
     dt = min(times)
+    # the fused kernel's roofline fraction on the slab batch, and the plain per-patch path
+    f = prism.Fitter(vh, opts, slabs=(30, 5))
+    f.step(3)
+    prof = f.profile(20)
+    shape = f.shape()
+    f.close()
+    flops = n_slab_vox * flops_per_voxel_iteration(vol.bvals, "mse", False, K_FIB, shape["shell_loop"])
+    peak, peak_src = fp32_peak_tflops()
+    achieved = flops / (prof["fused_ms"] / 1e3) / 1e12
+    unfused = None
+    if not args.no_unfused:
+        plain = prism.options(K=K_FIB, loss="mse", patch_dim=16, lam_orphan=0.01, lam_order=0.01, optimizer="rprop",
+                              fused=0, use_graph=0, **PRIORS)
+        fu = prism.Fitter(vh, plain, slabs=(30, 5))
+        fu.step(1)
+        fu.sync()
+        u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        u0.record()
+        fu.step(2)
+        u1.record()
+        fu.sync()
+        ms_u = u0.elapsed_time(u1) / 2
+        fu.close()
+        unfused = {"value": n_slab_vox / (ms_u / 1e3), "ms_per_step": ms_u, "steps": 2,
+                   "unit": "slab voxel-iterations/s"}
     line = {"workload": "hcp_shaped_brain_slabs_30_overlap_5_K3_mse_full_priors_rprop_100_iterations",
             "voxels": int(s0.shape[0]), "slabs": n_slabs, "slab_voxels": n_slab_vox, "iterations": iters,
             "seconds": dt, "value": n_slab_vox * iters / dt, "unit": "slab voxel-iterations/s",
             "timing": "wall clock, pinned host signal, set-up + iterations + stitch + read-out, best of 2",
+            "profile_ms": prof, "launch": shape,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "kernel": "k_iter_fused", "peak_source": "derived: " + peak_src},
+            "unfused": unfused,
+            "speedup_vs_unfused": (unfused["ms_per_step"] / (prof["iter_ms"])) if unfused else None,
             "paper_context": "the paper reports about 12 minutes for this pipeline on an RTX A6000"}
     print(json.dumps(line), flush=True)
     return 0
@@ -507,9 +684,15 @@ def run_disco(args):
         V = f.n_vox
         f.close()
     dt = min(times)
+    vdev = types.SimpleNamespace(mask=vol.mask, signal=torch.as_tensor(vol.signal, device="cuda"), bvals=vol.bvals,
+                                 bvecs=vol.bvecs, init=None)
+    leg = speed_leg([vdev], dict(K=5, loss="nll", patch_dim=16, lam_orphan=0.01, lam_order=0.01, **PRIORS), 100, 5,
+                    unfused_steps=0 if args.no_unfused else 2)
     line = {"workload": "disco1_shaped_40cubed_N364_K5_nll_priors_300_iterations", "voxels": V, "iterations": iters,
             "seconds": dt, "value": V * iters / dt, "unit": "voxel-iterations/s", "profile_ms": prof,
-            "timing": "wall clock, pinned host signal, set-up + iterations + read-out, best of 2"}
+            "timing": "wall clock, pinned host signal, set-up + iterations + read-out, best of 2",
+            "graph_replay": {k: leg[k] for k in ("value", "ms_per_step", "launch", "roofline")},
+            "unfused": leg.get("unfused"), "speedup_vs_unfused": leg.get("speedup_vs_unfused")}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -534,12 +717,31 @@ def run_crossing(args):
             f.sync()
             d, _, pk = f.fibers(0.15)
             per, overall, rec, prec, f1 = crossing.score(d, pk, vol.gt["dirs"], vol.gt["ffib"], vol.gt["case"])
+            final_loss = float(f.loss()[0])
+            prof = f.profile(10)
+            shape = f.shape()
+            flops = f.n_vox * flops_per_voxel_iteration(vol.bvals, loss, False, CROSS_OPTS["K"], shape["shell_loop"])
+            peak, _ = fp32_peak_tflops()
+            roof = {"bound": "alu", "achieved": flops / (prof["fused_ms"] / 1e3) / 1e12, "peak": peak,
+                    "unit": "TFLOP/s", "kernel": "k_iter_fused"}
+            roof["frac"] = roof["achieved"] / peak
+            fu = prism.Fitter(vol, prism.options(loss=loss, fused=0, use_graph=0, **CROSS_OPTS))
+            fu.step(1)
+            fu.sync()
+            u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            u0.record()
+            fu.step(5)
+            u1.record()
+            fu.sync()
+            unfused_ms = u0.elapsed_time(u1) / 5
+            fu.close()
             line = {"workload": "crossing_benchmark_N193_K2", "snr": snr, "loss": loss, "voxels": f.n_vox,
                     "iterations": args.cross_iters, "fit_ms": e0.elapsed_time(e1),
                     "single_fiber_deg": per[0],
                     "per_angle_deg": {str(a): per[i + 1] for i, a in enumerate(P.BENCH_ANGLES)},
                     "overall_deg": overall, "recall": rec, "precision": prec, "f1": f1,
-                    "final_loss": float(f.loss()[0])}
+                    "final_loss": final_loss, "profile_ms": prof, "launch": shape, "roofline": roof,
+                    "unfused_ms_per_step": unfused_ms, "speedup_vs_unfused": unfused_ms / prof["iter_ms"]}
             print(json.dumps(line), flush=True)
             f.close()
     return 0
@@ -563,10 +765,12 @@ def main():
     ap.add_argument("--no-unfused", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="brain", choices=["brain", "crossing", "bundle", "multi", "slabs", "disco"],
-                    help="crossing: fit quality on the crossing-fiber benchmark layout; bundle / multi: "
-                         "speed of the calibrated NLL configurations; slabs: the whole-brain slab "
-                         "pipeline; disco: the DiSCo1-shaped K = 5 NLL fit (not the headline)")
+    ap.add_argument("--workload", default="brain",
+                    choices=["brain", "crossing", "bundle", "multi", "slabs", "disco", "patch", "sweep"],
+                    help="crossing: fit quality on the crossing-fiber benchmark layout; patch / sweep: speed "
+                         "on the 8^3 crossing patch and the 16-volume crossing sweep; bundle / multi: speed "
+                         "of the calibrated NLL configurations; slabs: the whole-brain slab pipeline; "
+                         "disco: the DiSCo1-shaped K = 5 NLL fit (none of these is the headline)")
     ap.add_argument("--cross-snr", type=float, nargs="+", default=[10.0, 30.0, 50.0])
     ap.add_argument("--cross-voxels", type=int, default=200, help="voxels per angle (and single-fiber controls)")
     ap.add_argument("--cross-iters", type=int, default=300)
@@ -575,6 +779,10 @@ def main():
         return run_crossing(args)
     if args.workload in ("bundle", "multi"):
         return run_calibrated(args)
+    if args.workload in ("patch", "sweep"):
+        if args.warmup < 3:
+            args.warmup = 3
+        return run_small(args)
     if args.workload == "slabs":
         return run_slabs(args)
     if args.workload == "disco":
