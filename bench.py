@@ -52,8 +52,9 @@ FLOPS_PER_B0_PAIR = 5
 # DRAM bytes per voxel-iteration of the fused kernel (read + write) from an ncu capture of the
 # scaled brain (traffic grows in proportion to the voxels), valid only for the kernel sources
 # whose SHA-256 is TRAFFIC_SOURCES_SHA256: any other hash reports the traffic as null.
-TRAFFIC_BYTES_PER_VOXEL_ITER = None
-TRAFFIC_SOURCES_SHA256 = None
+# 212,900 voxels: 387.1 and 381.7 MB in two launches (profiles/k_iter_fused_hcp_brain_dram_traffic.md).
+TRAFFIC_BYTES_PER_VOXEL_ITER = 1806.0
+TRAFFIC_SOURCES_SHA256 = "5ea6b0448a4c82cd32e18a18676f3aba4bea4937f3cd978d0350b46223c4ddf9"
 FUSED_SOURCES = ("prism_kernels.cuh", "prism_device.cuh", "prism_kset.cuh", "bessel_fit.h", "prism_k3.cu")
 # FP32 lanes per SM on GB300 (4 sub-partitions x 32); the peak multiplies them by the device's
 # SM count, 2 flops per fused multiply-add and the maximum SM clock seen by nvidia-smi.
@@ -513,9 +514,9 @@ def run_ours(args):
             torch.set_num_threads(nt)
         cpu["value_1core"] = rate1
         cpu["sample_1core"] = f"1 fullest 16^3 patch ({nvox1} voxels) x 5 iterations, {dt1:.1f} s"
-    # per iteration: neighbour-prior preparation (+ the neighbour-prior rows with several lanes
-    # per voxel) + fused kernel (groups finalised inside it)
-    launches = 1 + (1 if PRIORS["lam_sp"] > 0 else 0) + (1 if tile["threads_per_voxel"] > 1 else 0)
+    # per iteration: the Huber-Laplacian preparation, the neighbour-prior rows and the fused
+    # kernel (groups finalised inside it)
+    launches = 1 + (1 if PRIORS["lam_sp"] > 0 else 0) + (1 if (PRIORS["lam_sp"] > 0 or PRIORS["lam_dir"] > 0) else 0)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "strong",

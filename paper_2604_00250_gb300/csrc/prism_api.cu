@@ -594,8 +594,14 @@ int build_plan(prism_handle* h, const prism_volume* vols, int n_vols, Plan& pl) 
       gr.gtab_off = static_cast<int32_t>(h->gtab.size());
       h->gtab.resize(h->gtab.size() + 3 * static_cast<size_t>(NPg), 0.f);
       float* gt = h->gtab.data() + gr.gtab_off;
-      for (int n = 0; n < v.n_meas; ++n)
-        for (int c = 0; c < 3; ++c) gt[c * NPg + n] = v.bvecs[3 * ord[n] + c];
+      // per pair p: {g_x(2p), g_x(2p+1), g_y(2p), g_y(2p+1)} at 4p, then g_z of every measurement
+      // from 2 NP on (one 16-byte and one 8-byte shared-memory load per pair)
+      for (int n = 0; n < v.n_meas; ++n) {
+        const int p = n / 2, h = n % 2;
+        gt[4 * p + h] = v.bvecs[3 * ord[n]];
+        gt[4 * p + 2 + h] = v.bvecs[3 * ord[n] + 1];
+        gt[2 * NPg + n] = v.bvecs[3 * ord[n] + 2];
+      }
     }
     tab += v.n_meas;
     gr.table2_off = static_cast<int32_t>(h->tab2_pairs);

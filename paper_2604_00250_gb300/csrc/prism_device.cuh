@@ -82,7 +82,7 @@ struct GroupDev {
   int32_t nb0p;        // leading table pairs whose two measurements both have b = 0 (see meas_order)
   int32_t run_off;     // first ShellRun of the group (shell loop)
   int32_t n_runs;      // its shells
-  int32_t gtab_off;    // float offset of the group's gradient table [3][NP] (g_x, g_y, g_z rows)
+  int32_t gtab_off;    // float offset of the group's gradient table: [NP / 2][4] {g_x, g_y} pairs, then [NP] g_z
   int32_t pad_;
 };
 
@@ -106,7 +106,7 @@ struct IterArgs {
   const uint32_t* vflag;   // [Vpad] bits 0-5 TV neighbours (+x,-x,+y,-y,+z,-z) masked; bits 8-12 |N(x)|
   const MeasRow* table;    // per-group measurement tables
   const MeasPair* table2;  // the same, paired (see MeasPair)
-  const float* gtab;       // per group [3][NP] gradient directions in table order (shell loop)
+  const float* gtab;       // per group gradient directions in table order (shell loop; see GroupDev)
   const ShellRun* runs;    // per group shells in table order (shell loop)
   const float* gparams;    // packed group parameters
   float* gU;               // [Vpad] dJ/dU(x)

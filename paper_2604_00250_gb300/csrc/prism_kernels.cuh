@@ -1229,8 +1229,8 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<K, TPV, LOSS,
       if constexpr (SHELL) {
         // pairs of this chunk, in segments that stay inside one shell (shells have even lengths)
         const float2* __restrict__ yc2 = reinterpret_cast<const float2*>(ring + s * (kChunk * VW)) + lv;
-        const float2* __restrict__ gx2 = reinterpret_cast<const float2*>(s_g);
-        const float2* __restrict__ gy2 = reinterpret_cast<const float2*>(s_g + NP);
+        // gradient rows: {g_x, g_y} of a pair as one float4, then the g_z pairs
+        const float4* __restrict__ gxy = reinterpret_cast<const float4*>(s_g);
         const float2* __restrict__ gz2 = reinterpret_cast<const float2*>(s_g + 2 * NP);
         const int pc0 = j * (kChunk / 2), pc1 = min(pc0 + kChunk / 2, N / 2);
         if (act) {
@@ -1256,7 +1256,10 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<K, TPV, LOSS,
             } else {
               // four steps in flight (2 % faster than two on the brain workload; no spills)
 #pragma unroll 4
-              for (; p < pe; ++p) shell_step(SS, gx2[p], gy2[p], gz2[p], yc2[(p - pc0) * VW]);
+              for (; p < pe; ++p) {
+                const float4 gq = gxy[p];
+                shell_step(SS, make_float2(gq.x, gq.y), make_float2(gq.z, gq.w), gz2[p], yc2[(p - pc0) * VW]);
+              }
             }
           }
         }
