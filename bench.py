@@ -38,11 +38,12 @@ PRIORS = dict(lam_rep=0.01, lam_sparse=0.02, lam_sp=0.01, lam_dir=0.005)
 
 # FP32 floating-point operations per (voxel, measurement) pair of the fused kernel's loop on
 # this workload (MSE, no calibration), fused multiply-add = 2.
-# Shell loop (every shell of the scheme even): per fiber 27 -- scaled cosine c' = d' . g 5,
+# Shell loop (every shell of the scheme even): per fiber 26 -- scaled cosine c' = d' . g 5,
 # exponent arguments 2 + 2, f_in e1 + (1 - f_in) p 1, T 2, the two adjoint sums 4, dE/dc
-# factor 3, its product with r c' 2, the direction sum 6 -- and per measurement 5 (residual 2,
-# its square 2, the shell's sum of r 1); the isotropic terms are formed once per shell.
-FLOPS_PER_PAIR_SHELL = 5 + 27 * K_FIB
+# factor f_in e1 + rho (1 - f_in) p 2 (the shell's factor ap is applied at shell changes), its
+# product with r c' 2, the direction sum 6 -- and per measurement 5 (residual 2, its square 2,
+# the shell's sum of r 1); the isotropic terms are formed once per shell.
+FLOPS_PER_PAIR_SHELL = 5 + 26 * K_FIB
 # Per-measurement loop: 17 per measurement (isotropic mixture 5, residual 2, its square 2,
 # isotropic adjoint 6, two derivative constants 2) + 28 per fiber.
 FLOPS_PER_PAIR = 17 + 28 * K_FIB
@@ -71,9 +72,9 @@ def flops_per_measurement(loss, cal, K, shell):
     y_hat = S0 T (1) and the NLL terms (71: z = y |y_hat| / sigma^2 2; Q(z) and L(z) from the
     fitted functions of 4/z, 55 -- two degree-12 Horner chains 48, the argument and scale 3,
     log terms 4; (y - |y_hat|)^2, y |y_hat| Q and L sums 9; dL/dy_hat 4; the rest 1) -- 85 + 28 K;
-    with calibration 94 + 28 K. Shell loop: 5 + 27 K (see FLOPS_PER_PAIR_SHELL)."""
+    with calibration 94 + 28 K. Shell loop: 5 + 26 K (see FLOPS_PER_PAIR_SHELL)."""
     if shell:
-        return 5 + 27 * K
+        return 5 + 26 * K
     if loss == "mse":
         return (28 + 28 * K) if cal else (17 + 28 * K)
     return (94 + 28 * K) if cal else (85 + 28 * K)

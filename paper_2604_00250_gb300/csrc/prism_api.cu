@@ -450,7 +450,6 @@ static bool shell_runs(const prism_volume& v, const int32_t* ord, std::vector<Sh
     const double s = std::sqrt(bd * dpar * L2E);
     r.s = static_cast<float>(s);
     r.ap = (s > 0.0) ? static_cast<float>(-2.0 * bd * dpar / s) : 0.f;
-    r.bp = (s > 0.0) ? static_cast<float>(2.0 * bd * (dperp - dpar) / s) : 0.f;
     runs.push_back(r);
     ++nr;
     n0 = n1;

@@ -744,7 +744,9 @@ __device__ __forceinline__ void block_reduce3(double v0, double v1, double v2, d
 //   m = c'^2 - log2 f_in,  f_in e1 = 2^(-m),  (1 - f_in) p = 2^(-rho m + Kp),
 //   T = T0 + sum_k f_k (f_in e1 + (1 - f_in) p),  r = y - S0 T  (two measurements per step).
 // The adjoint sums are ga_k = sum r f_in e1, gb_k = sum r (1 - f_in) p and
-// gd_k = sum r c' (ap f_in e1 + bp (1 - f_in) p) g = sum r dE_wm,k/dc g.
+// gd_k = sum r dE_wm,k/dc g = sum_shells ap sum_n r c' (f_in e1 + rho (1 - f_in) p) g; the
+// shell's factor ap is not applied per step: gd holds the sum divided by the current shell's
+// ap and is rescaled by ap_old / ap_new when a shell with b > 0 opens (apc is the current ap).
 // Per-voxel scalars needed only at shell changes sit in a per-thread column of shared memory.
 // ---------------------------------------------------------------------------
 constexpr int kFusedThreadsShell = 128;   // threads of the fused kernel's CTA (kFusedThreads)
@@ -757,7 +759,7 @@ struct ShellState {
   float2 nS0;           // -S0
   float2 T0;            // isotropic mixture of the shell (b = 0: the sum of all fractions)
   float2 Kp;            // C0 - b D_perp log2(e)
-  float2 ap, bp;        // the shell's ap, bp
+  float apc;            // ap of the last shell with b > 0 (the scale of gd)
   float2 l1, Qs;        // sum r^2; sum r over the current shell
   float2 ga[K], gb[K];
   float2 gd[K][3];
@@ -774,7 +776,7 @@ struct ShellRows {
 
 template <int K>
 __device__ __forceinline__ void shell_step(ShellState<K>& S, float2 gx, float2 gy, float2 gz, float2 y) {
-  const float2 nrho = make_float2(-kRho, -kRho);
+  const float2 nrho = make_float2(-kRho, -kRho), rho = make_float2(kRho, kRho);
   float2 cp[K], e1[K], pp[K], t[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -794,7 +796,7 @@ __device__ __forceinline__ void shell_step(ShellState<K>& S, float2 gx, float2 g
   for (int k = 0; k < K; ++k) {
     S.ga[k] = __ffma2_rn(r, e1[k], S.ga[k]);
     S.gb[k] = __ffma2_rn(r, pp[k], S.gb[k]);
-    const float2 inner = __ffma2_rn(S.bp, pp[k], __fmul2_rn(S.ap, e1[k]));
+    const float2 inner = __ffma2_rn(rho, pp[k], e1[k]);
     const float2 w = __fmul2_rn(__fmul2_rn(r, cp[k]), inner);
     S.gd[k][0] = __ffma2_rn(w, gx, S.gd[k][0]);
     S.gd[k][1] = __ffma2_rn(w, gy, S.gd[k][1]);
@@ -836,8 +838,14 @@ __device__ __forceinline__ void shell_open(ShellState<K>& S, const ShellRun& R, 
   }
   S.T0 = dup2(T0);
   S.Kp = dup2(col[SR::c0 * C] + R.nbperp);
-  S.ap = dup2(R.ap);
-  S.bp = dup2(R.bp);
+  if (!R.b0) {
+    const float2 sc = dup2(S.apc / R.ap);
+    S.apc = R.ap;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) S.gd[k][c] = __fmul2_rn(S.gd[k][c], sc);
+  }
 #pragma unroll
   for (int k = 0; k < K; ++k)
 #pragma unroll
@@ -873,6 +881,7 @@ __device__ __forceinline__ void shell_begin(ShellState<K>& S, const Vox<K>& P, f
     S.ga[k] = S.gb[k] = z;
     S.gd[k][0] = S.gd[k][1] = S.gd[k][2] = z;
   }
+  S.apc = 1.f;
   S.ri = -1;
   S.pend = 0;
   S.b0 = 0;
@@ -894,7 +903,7 @@ __device__ __forceinline__ void shell_fold(const Vox<K>& P, const ShellState<K>&
     A.gwa[k] = -(S.ga[k].x + S.ga[k].y);
     A.gwb[k] = -(S.gb[k].x + S.gb[k].y);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) A.gd[k][c] = -(S.gd[k][c].x + S.gd[k][c].y);
+    for (int c = 0; c < 3; ++c) A.gd[k][c] = -S.apc * (S.gd[k][c].x + S.gd[k][c].y);
     g = fmaf(P.f[2 + k], A.gwa[k] + A.gwb[k], g);
   }
   A.gS0 = g;
