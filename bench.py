@@ -53,9 +53,9 @@ FLOPS_PER_B0_PAIR = 5
 # DRAM bytes per voxel-iteration of the fused kernel (read + write) from an ncu capture of the
 # scaled brain (traffic grows in proportion to the voxels), valid only for the kernel sources
 # whose SHA-256 is TRAFFIC_SOURCES_SHA256: any other hash reports the traffic as null.
-# 212,900 voxels: 387.1 and 381.7 MB in two launches (profiles/k_iter_fused_hcp_brain_dram_traffic.md).
-TRAFFIC_BYTES_PER_VOXEL_ITER = 1806.0
-TRAFFIC_SOURCES_SHA256 = "5ea6b0448a4c82cd32e18a18676f3aba4bea4937f3cd978d0350b46223c4ddf9"
+# 212,900 voxels: 385.2 and 384.5 MB in two launches (profiles/k_iter_fused_hcp_brain_dram_traffic.md).
+TRAFFIC_BYTES_PER_VOXEL_ITER = 1807.7
+TRAFFIC_SOURCES_SHA256 = "65ed460f8bb1e30ee76a0cdbad15885be032b8ac256eae1a746dabd1213ab99b"
 FUSED_SOURCES = ("prism_kernels.cuh", "prism_device.cuh", "prism_kset.cuh", "bessel_fit.h", "prism_k3.cu")
 # FP32 lanes per SM on GB300 (4 sub-partitions x 32); the peak multiplies them by the device's
 # SM count, 2 flops per fused multiply-add and the maximum SM clock seen by nvidia-smi.
