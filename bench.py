@@ -480,8 +480,9 @@ def run_ours(args):
         keep = []
         arr, nv = prism._volumes_array([vhost], keep)
         loss_out = np.empty(1, dtype=np.float64)
-        # three complete calls, the fastest reported and all listed: on the shared GB300 hosts
-        # the wall time of a call varies by up to 12 % (the device time of its iterations does not)
+        # three complete calls, the median reported, the fastest and all three listed: on the
+        # shared GB300 hosts the wall time of a call varies by up to 15 % (the device time of its
+        # iterations does not)
         runs = []
         for _ in range(3):
             barrier()

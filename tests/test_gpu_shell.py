@@ -8,6 +8,7 @@ Checked here, on schemes whose measurements arrive interleaved in the caller's o
 - the first iteration's gradient (Adam's first moment) per block against the oracle's;
 - three iterations against the oracle's trajectory, and against the per-measurement loop of
   the same library (shells = -1);
+- a scheme without b = 0 whose shells span b = 5 to 6000 (the direction sums' rescaling);
 - the shapes that cannot take the loop fall back to the per-measurement loop (an odd shell,
   more than 16 shells) and still match the oracle.
 """
@@ -84,6 +85,31 @@ def test_shell_loop_trajectory_matches_oracle_and_the_measurement_loop(K):
     assert float(np.max(np.abs(g.params_host() - th))) < 3e-4
     np.testing.assert_allclose(g.loss_history(), res.loss_history, rtol=1e-5)
     g.close()
+
+
+def test_shell_loop_without_b0_and_with_a_low_b_shell():
+    """No b = 0 measurement: the first shell the loop opens has b > 0, and a b = 5 shell next to
+    b = 6000 gives the largest ratio between two shells' dE/dc factors (ap is proportional to
+    sqrt(b)), by which the direction sums are rescaled at each shell change. The b = 5 shell
+    also serves as the b0 reference of the normalisation (b <= 50)."""
+    K = 3
+    sch = P.make_scheme(0, [(5, 4), (1000, 6), (6000, 8)], 5)
+    v = P.random_volume((6, 5, 4), scheme=sch, seed=11, mask_density=0.8)
+    vols = [_shuffled(v, 6)]
+    rng = np.random.default_rng(77)
+    inits = [(t + rng.normal(0, 0.3, t.shape)).astype(np.float32) for t in inits_for(vols, K, 2)]
+    f, ovs = make_pair(vols, inits, K=K, **KW)
+    assert f.shape()["shell_loop"] == 1
+    gps = split_groups(f.groups(), f)
+    f.step(1)
+    f.sync()
+    g_vox, _ = fused_gradient(f, f.opts.beta1)
+    J, _, g, _ = O.value_and_grad(ovs[0], torch.as_tensor(inits[0]).double(), gps[0])
+    assert abs(f.loss_history()[0, 0] - float(J)) <= TOL_LOSS * abs(float(J))
+    for name, sl in block_slices(K).items():
+        e = normwise(g_vox[:, sl], g[:, sl].numpy())
+        assert e <= TOL_GRAD, (name, e)
+    f.close()
 
 
 @pytest.mark.parametrize("scheme", ["odd_shell", "many_shells"])
