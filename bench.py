@@ -38,18 +38,20 @@ PRIORS = dict(lam_rep=0.01, lam_sparse=0.02, lam_sp=0.01, lam_dir=0.005)
 
 # FP32 floating-point operations per (voxel, measurement) pair of the fused kernel's loop on
 # this workload (MSE, no calibration), fused multiply-add = 2.
-# Shell loop (every shell of the scheme even): per fiber 26 -- scaled cosine c' = d' . g 5,
-# exponent arguments 2 + 2, f_in e1 + (1 - f_in) p 1, T 2, the two adjoint sums 4, dE/dc
-# factor f_in e1 + rho (1 - f_in) p 2 (the shell's factor ap is applied at shell changes), its
-# product with r c' 2, the direction sum 6 -- and per measurement 5 (residual 2, its square 2,
-# the shell's sum of r 1); the isotropic terms are formed once per shell.
-FLOPS_PER_PAIR_SHELL = 5 + 26 * K_FIB
+# Shell loop (every shell of the scheme even): per fiber 26 -- scaled cosine c' = d . g' 5,
+# exponent arguments 2 + 2, f_in e1 + (1 - f_in) p 1, its product with -S0 f_k into the residual
+# 2, the two adjoint sums 4, dE/dc factor f_in e1 + rho (1 - f_in) p 2, its product with r c' 2,
+# the direction sum 6 -- and per measurement 4 (y - S0 T0 1, the residual's square 2, the
+# shell's sum of r 1); the isotropic terms are formed once per shell.
+FLOPS_PER_PAIR_SHELL = 4 + 26 * K_FIB
 # Per-measurement loop: 17 per measurement (isotropic mixture 5, residual 2, its square 2,
 # isotropic adjoint 6, two derivative constants 2) + 28 per fiber.
 FLOPS_PER_PAIR = 17 + 28 * K_FIB
 # Measurements with b = 0 (leading the table) need no fiber terms: r = y - S0 sum(f) and r^2
-# (two multiply-adds) and the running sum of r (one add).
+# (two multiply-adds) and the running sum of r (one add); in the shell loop r = y + (-S0 T0) is
+# one add.
 FLOPS_PER_B0_PAIR = 5
+FLOPS_PER_B0_PAIR_SHELL = 4
 # DRAM bytes per voxel-iteration of the fused kernel (read + write) from an ncu capture of the
 # scaled brain (traffic grows in proportion to the voxels), valid only for the kernel sources
 # whose SHA-256 is TRAFFIC_SOURCES_SHA256: any other hash reports the traffic as null.
@@ -72,17 +74,17 @@ def flops_per_measurement(loss, cal, K, shell):
     y_hat = S0 T (1) and the NLL terms (71: z = y |y_hat| / sigma^2 2; Q(z) and L(z) from the
     fitted functions of 4/z, 55 -- two degree-12 Horner chains 48, the argument and scale 3,
     log terms 4; (y - |y_hat|)^2, y |y_hat| Q and L sums 9; dL/dy_hat 4; the rest 1) -- 85 + 28 K;
-    with calibration 94 + 28 K. Shell loop: 5 + 26 K (see FLOPS_PER_PAIR_SHELL)."""
+    with calibration 94 + 28 K. Shell loop: 4 + 26 K (see FLOPS_PER_PAIR_SHELL)."""
     if shell:
-        return 5 + 26 * K
+        return 4 + 26 * K
     if loss == "mse":
         return (28 + 28 * K) if cal else (17 + 28 * K)
     return (94 + 28 * K) if cal else (85 + 28 * K)
 
 
 def flops_per_voxel_iteration(bvals, loss, cal, K, shell):
-    """Per voxel of one volume: b = 0 measurements cost FLOPS_PER_B0_PAIR where the loop takes
-    them apart (MSE without calibration: the shell loop's b = 0 shell, or the leading b = 0
+    """Per voxel of one volume: b = 0 measurements cost FLOPS_PER_B0_PAIR(_SHELL) where the loop
+    takes them apart (MSE without calibration: the shell loop's b = 0 shell, or the leading b = 0
     pairs of the per-measurement loop); every other measurement the loop's full cost."""
     bv = np.asarray(bvals)
     n0 = int(np.count_nonzero(bv == 0))
@@ -90,7 +92,8 @@ def flops_per_voxel_iteration(bvals, loss, cal, K, shell):
         nb0 = n0 if shell else 2 * (n0 // 2)
     else:
         nb0 = 0
-    return (len(bv) - nb0) * flops_per_measurement(loss, cal, K, shell) + nb0 * FLOPS_PER_B0_PAIR
+    per_b0 = FLOPS_PER_B0_PAIR_SHELL if shell else FLOPS_PER_B0_PAIR
+    return (len(bv) - nb0) * flops_per_measurement(loss, cal, K, shell) + nb0 * per_b0
 
 
 def fp32_peak_tflops(device_index=0):
@@ -435,7 +438,8 @@ def run_ours(args):
     nb0 = 2 * (int(np.count_nonzero(np.asarray(vol.bvals) == 0)) // 2)
     shape = f.shape()
     per_pair = FLOPS_PER_PAIR_SHELL if shape["shell_loop"] else FLOPS_PER_PAIR
-    achieved = V * ((N - nb0) * per_pair + nb0 * FLOPS_PER_B0_PAIR) / (fused_ms / 1e3) / 1e12
+    per_b0 = FLOPS_PER_B0_PAIR_SHELL if shape["shell_loop"] else FLOPS_PER_B0_PAIR
+    achieved = V * ((N - nb0) * per_pair + nb0 * per_b0) / (fused_ms / 1e3) / 1e12
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max_mhz = ck.get("sm_max_mhz") or 2070.0
     peak = n_sm * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
@@ -529,7 +533,7 @@ def run_ours(args):
                                        "brain_scale": args.brain_scale, "launch": tile}),
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                              "frac": achieved / peak, "traffic": traffic,
-                             "flops_per_voxel_iteration": (N - nb0) * per_pair + nb0 * FLOPS_PER_B0_PAIR,
+                             "flops_per_voxel_iteration": (N - nb0) * per_pair + nb0 * per_b0,
                              "traffic_unit": "bytes per launch (ncu dram read + write, scaled capture)",
                              "kernel": "k_iter_fused", "kernel_ms": fused_ms,
                              "peak_source": f"derived: {n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "

@@ -312,7 +312,7 @@ int prism_fit(const prism_volume* vols, int32_t n_vols, const prism_options* opt
  * refuses with E_NONFINITE) is reported in the outputs instead: its gradient row and the
  * loss are NaN; the other rows are computed as usual.
  * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture begins.
+ * (cudaGetSymbolAddress).
  * Every call shares the array and leaves its contents behind (it clears what must start
  * at zero itself), so two calls whose GPU work overlaps on the same device (for example
  * on two streams) race with each other: serialise them.

@@ -425,12 +425,15 @@ static int32_t meas_order(const prism_volume& v, bool cal, std::vector<int32_t>&
   return nz / 2;
 }
 
+// The fiber model's fixed diffusivities (Eq. 5, mm^2/s) and log2(e), for the shell loop's
+// host-side constants.
+constexpr double kDpar = 1.7e-3, kDperp = 0.4e-3, kLog2e = 1.4426950408889634;
+
 // Shells of one group in table order (runs of equal b-value) with the constants of the
 // shell loop (ShellRun); false when a shell holds an odd number of measurements (a pair would
 // straddle two shells) or there are more than kMaxRuns shells.
 static bool shell_runs(const prism_volume& v, const int32_t* ord, std::vector<ShellRun>& runs) {
   const int N = v.n_meas;
-  const double L2E = 1.4426950408889634, dpar = 1.7e-3, dperp = 0.4e-3;   // Eq. 5, mm^2/s
   bool ok = true;
   int n0 = 0, nr = 0;
   while (n0 < N) {
@@ -446,10 +449,7 @@ static bool shell_runs(const prism_volume& v, const int32_t* ord, std::vector<Sh
     r.ecsf = static_cast<float>(std::exp(-bd * 3.0e-3));   // Eq. 4
     r.egm = static_cast<float>(std::exp(-bd * 0.9e-3));
     r.eres = static_cast<float>(std::exp(-bd * 0.2e-3));
-    r.nbperp = static_cast<float>(-bd * dperp * L2E);
-    const double s = std::sqrt(bd * dpar * L2E);
-    r.s = static_cast<float>(s);
-    r.ap = (s > 0.0) ? static_cast<float>(-2.0 * bd * dpar / s) : 0.f;
+    r.nbperp = static_cast<float>(-bd * kDperp * kLog2e);
     runs.push_back(r);
     ++nr;
     n0 = n1;
@@ -593,13 +593,15 @@ int build_plan(prism_handle* h, const prism_volume* vols, int n_vols, Plan& pl) 
       gr.gtab_off = static_cast<int32_t>(h->gtab.size());
       h->gtab.resize(h->gtab.size() + 3 * static_cast<size_t>(NPg), 0.f);
       float* gt = h->gtab.data() + gr.gtab_off;
-      // per pair p: {g_x(2p), g_x(2p+1), g_y(2p), g_y(2p+1)} at 4p, then g_z of every measurement
+      // the scaled directions g' = s g, s = sqrt(b D_par log2 e) (Eq. 5: c' = s c = g' . d), per
+      // pair p: {g'_x(2p), g'_x(2p+1), g'_y(2p), g'_y(2p+1)} at 4p, then g'_z of every measurement
       // from 2 NP on (one 16-byte and one 8-byte shared-memory load per pair)
       for (int n = 0; n < v.n_meas; ++n) {
         const int p = n / 2, h = n % 2;
-        gt[4 * p + h] = v.bvecs[3 * ord[n]];
-        gt[4 * p + 2 + h] = v.bvecs[3 * ord[n] + 1];
-        gt[2 * NPg + n] = v.bvecs[3 * ord[n] + 2];
+        const double s = std::sqrt(static_cast<double>(v.bvals[ord[n]]) * kDpar * kLog2e);
+        gt[4 * p + h] = static_cast<float>(s * v.bvecs[3 * ord[n]]);
+        gt[4 * p + 2 + h] = static_cast<float>(s * v.bvecs[3 * ord[n] + 1]);
+        gt[2 * NPg + n] = static_cast<float>(s * v.bvecs[3 * ord[n] + 2]);
       }
     }
     tab += v.n_meas;
@@ -948,7 +950,7 @@ int init_impl(prism_handle* h, const prism_volume* vols, int n_vols, const std::
   const size_t ring = static_cast<size_t>(kStages) * kChunk * (kFusedThreads / h->TPV) * sizeof(float);
   if (h->shell) {
     h->fused_smem = 3 * static_cast<size_t>(h->Nmax) * sizeof(float) + kMaxRuns * sizeof(ShellRun) +
-                    static_cast<size_t>(3 * o.K + 9) * kFusedThreads * sizeof(float) + ring;
+                    static_cast<size_t>(kShellCols) * kFusedThreads * sizeof(float) + ring;
   } else {
     h->fused_smem = static_cast<size_t>(h->Nmax) * sizeof(MeasRow) + ring +
                     (h->cal ? kNGrid * sizeof(float) + static_cast<size_t>(NW) * 2 * h->Nmax * sizeof(float) : 0);

@@ -46,20 +46,20 @@ struct __align__(16) MeasPair {
 constexpr int kPairFieldA = 11, kPairFieldBeta = 12;
 
 // One run of equal b-values in a group's table order (a shell), for the shell loop of the fused
-// kernel (one thread per voxel, MSE, no calibration): measurement pairs [p0, p1), the isotropic
-// decays of Eq. 4 at this b, and the shell's constants of the scaled fiber terms (Eq. 5 with
-// c' = s c, s = sqrt(b D_par log2 e)):
+// kernel (one thread per voxel, MSE, no calibration): measurement pairs [p0, p1) and the
+// isotropic decays of Eq. 4 at this b. The fiber terms (Eq. 5) use the scaled cosine
+// c' = s c = g' . d with s = sqrt(b D_par log2 e) and g' = s g (the shell loop's gradient table):
 //   f_in e1 = 2^(log2 f_in - c'^2),   (1 - f_in) p = 2^(rho (log2 f_in - c'^2) + C0 - b D_perp log2 e)
 // with rho = 1 - D_perp / D_par and C0 = log2(1 - f_in) - rho log2 f_in per voxel, and
-//   dE_wm/dc = (c' / s) (A_n f_in e1 + B_n (1 - f_in) p) = c' ap (f_in e1 + rho (1 - f_in) p),
-// ap = A_n / s = -2 b D_par / s = -2 ln(2) s, since B_n = rho A_n.
+//   dE_wm/dd = -2 ln(2) c' (f_in e1 + rho (1 - f_in) p) g'.
 struct __align__(16) ShellRun {
   int32_t p0, p1, b0, pad;         // pairs [p0, p1); b0 = 1 for b = 0 (every E of Eqs. 4-5 is 1)
   float ecsf, egm, eres, nbperp;   // E_csf, E_gm, E_res; -b D_perp log2(e)
-  float s, ap, pad2, pad3;         // sqrt(b D_par log2 e); -2 b D_par / s (0 at b = 0)
 };
 constexpr int kMaxRuns = 16;        // shells per group the shell loop takes
+constexpr int kShellCols = 10;      // per-thread shared-memory column of the shell loop (floats)
 constexpr float kRho = 1.f - 0.4f / 1.7f;   // 1 - D_perp / D_par (Eq. 5)
+constexpr float kTwoLn2 = 1.3862943611198906f;   // 2 ln 2: d(2^(-x^2))/dx = -2 ln 2 x 2^(-x^2)
 
 // A tile: up to TV voxels of one patch, processed by one CTA.
 struct Tile {

@@ -740,38 +740,35 @@ __device__ __forceinline__ void block_reduce3(double v0, double v1, double v2, d
 // b-value order, so runs of equal b (shells, ShellRun) share Eq. 4's isotropic decays and Eq.
 // 5's exponent constants. Per shell and voxel the isotropic mixture T0 is formed once and the
 // isotropic adjoint sums need only sum_n r over the shell; per measurement and fiber the two
-// exponentials come from the scaled cosine c' = s c (see ShellRun):
+// exponentials come from the scaled cosine c' = g' . d of the table's g' = s g (see ShellRun):
 //   m = c'^2 - log2 f_in,  f_in e1 = 2^(-m),  (1 - f_in) p = 2^(-rho m + Kp),
-//   T = T0 + sum_k f_k (f_in e1 + (1 - f_in) p),  r = y - S0 T  (two measurements per step).
+//   r = y - S0 T = (y - S0 T0) - sum_k S0 f_k (f_in e1 + (1 - f_in) p)  (two measurements per step).
 // The adjoint sums are ga_k = sum r f_in e1, gb_k = sum r (1 - f_in) p and
-// gd_k = sum r dE_wm,k/dc g = sum_shells ap sum_n r c' (f_in e1 + rho (1 - f_in) p) g; the
-// shell's factor ap is not applied per step: gd holds the sum divided by the current shell's
-// ap and is rescaled by ap_old / ap_new when a shell with b > 0 opens (apc is the current ap).
+// gd_k = sum r c' (f_in e1 + rho (1 - f_in) p) g', which is -1 / (2 ln 2) times sum r dE_wm,k/dd.
 // Per-voxel scalars needed only at shell changes sit in a per-thread column of shared memory.
 // ---------------------------------------------------------------------------
 constexpr int kFusedThreadsShell = 128;   // threads of the fused kernel's CTA (kFusedThreads)
 
 template <int K>
 struct ShellState {
-  float2 f[K];          // fiber fractions f_wm,k (duplicated)
-  float2 dp[K][3];      // s d_k of the current shell
+  float2 nf[K];         // -S0 f_wm,k (duplicated)
+  float2 dp[K][3];      // d_k (duplicated)
   float2 nlfin;         // -log2 f_in
-  float2 nS0;           // -S0
-  float2 T0;            // isotropic mixture of the shell (b = 0: the sum of all fractions)
+  float2 c0;            // -S0 T0, T0 the shell's isotropic mixture (b = 0: the sum of all fractions)
   float2 Kp;            // C0 - b D_perp log2(e)
-  float apc;            // ap of the last shell with b > 0 (the scale of gd)
   float2 l1, Qs;        // sum r^2; sum r over the current shell
   float2 ga[K], gb[K];
   float2 gd[K][3];
   int ri, pend, b0;     // current shell, its end pair, b = 0 flag
 };
 
-// Rows of a thread's shared-memory column (stride kFusedThreads): d_k (3K), f_csf, f_gm,
-// f_res, f_in, 1 - f_in, C0, then the sums sum_n r E_csf, sum_n r E_gm, sum_n r E_res.
+// Rows of a thread's shared-memory column (stride kFusedThreads): S0, f_csf, f_gm, f_res, f_in,
+// 1 - f_in, C0, then the sums sum_n r E_csf, sum_n r E_gm, sum_n r E_res.
 template <int K>
 struct ShellRows {
-  static constexpr int dir = 0, fcsf = 3 * K, fgm = 3 * K + 1, fres = 3 * K + 2, fin = 3 * K + 3, omf = 3 * K + 4,
-                       c0 = 3 * K + 5, gcsf = 3 * K + 6, ggm = 3 * K + 7, gres = 3 * K + 8, count = 3 * K + 9;
+  static constexpr int s0 = 0, fcsf = 1, fgm = 2, fres = 3, fin = 4, omf = 5, c0 = 6, gcsf = 7, ggm = 8, gres = 9,
+                       count = kShellCols;
+  static_assert(gres < count, "the column holds every row");
 };
 
 template <int K>
@@ -786,10 +783,9 @@ __device__ __forceinline__ void shell_step(ShellState<K>& S, float2 gx, float2 g
     pp[k] = ex2_2(__ffma2_rn(nrho, m, S.Kp));
     t[k] = __fadd2_rn(e1[k], pp[k]);
   }
-  float2 T = __ffma2_rn(S.f[0], t[0], S.T0);
+  float2 r = __fadd2_rn(y, S.c0);   // y - y_hat
 #pragma unroll
-  for (int k = 1; k < K; ++k) T = __ffma2_rn(S.f[k], t[k], T);
-  const float2 r = __ffma2_rn(S.nS0, T, y);   // y - y_hat
+  for (int k = 0; k < K; ++k) r = __ffma2_rn(S.nf[k], t[k], r);
   S.l1 = __ffma2_rn(r, r, S.l1);
   S.Qs = __fadd2_rn(S.Qs, r);
 #pragma unroll
@@ -831,25 +827,14 @@ __device__ __forceinline__ void shell_open(ShellState<K>& S, const ShellRun& R, 
   constexpr int C = kFusedThreadsShell;
   S.pend = R.p1;
   S.b0 = R.b0;
-  float T0 = fmaf(col[SR::fcsf * C], R.ecsf, fmaf(col[SR::fgm * C], R.egm, col[SR::fres * C] * R.eres));
+  const float T0 = fmaf(col[SR::fcsf * C], R.ecsf, fmaf(col[SR::fgm * C], R.egm, col[SR::fres * C] * R.eres));
+  float c0 = -col[SR::s0 * C] * T0;
   if (R.b0) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) T0 += S.f[k].x;
+    for (int k = 0; k < K; ++k) c0 += S.nf[k].x;
   }
-  S.T0 = dup2(T0);
+  S.c0 = dup2(c0);
   S.Kp = dup2(col[SR::c0 * C] + R.nbperp);
-  if (!R.b0) {
-    const float2 sc = dup2(S.apc / R.ap);
-    S.apc = R.ap;
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) S.gd[k][c] = __fmul2_rn(S.gd[k][c], sc);
-  }
-#pragma unroll
-  for (int k = 0; k < K; ++k)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) S.dp[k][c] = dup2(R.s * col[(SR::dir + 3 * k + c) * C]);
 }
 
 // Voxel set-up of the shell loop from the transformed parameters (its column and registers).
@@ -859,14 +844,14 @@ __device__ __forceinline__ void shell_begin(ShellState<K>& S, const Vox<K>& P, f
   constexpr int C = kFusedThreadsShell;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    S.f[k] = dup2(P.f[2 + k]);
+    S.nf[k] = dup2(-P.S0 * P.f[2 + k]);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) col[(SR::dir + 3 * k + c) * C] = P.d[k][c];
+    for (int c = 0; c < 3; ++c) S.dp[k][c] = dup2(P.d[k][c]);
   }
   // log2 f_in and log2(1 - f_in), floored so that a saturated f_in gives no inf - inf
   const float lfin = fmaxf(lg2f_(P.fin), -40.f), lomf = fmaxf(lg2f_(P.omf), -126.f);
   S.nlfin = dup2(-lfin);
-  S.nS0 = dup2(-P.S0);
+  col[SR::s0 * C] = P.S0;
   col[SR::fcsf * C] = P.f[0];
   col[SR::fgm * C] = P.f[1];
   col[SR::fres * C] = P.f[K + 2];
@@ -881,7 +866,6 @@ __device__ __forceinline__ void shell_begin(ShellState<K>& S, const Vox<K>& P, f
     S.ga[k] = S.gb[k] = z;
     S.gd[k][0] = S.gd[k][1] = S.gd[k][2] = z;
   }
-  S.apc = 1.f;
   S.ri = -1;
   S.pend = 0;
   S.b0 = 0;
@@ -903,7 +887,7 @@ __device__ __forceinline__ void shell_fold(const Vox<K>& P, const ShellState<K>&
     A.gwa[k] = -(S.ga[k].x + S.ga[k].y);
     A.gwb[k] = -(S.gb[k].x + S.gb[k].y);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) A.gd[k][c] = -S.apc * (S.gd[k][c].x + S.gd[k][c].y);
+    for (int c = 0; c < 3; ++c) A.gd[k][c] = kTwoLn2 * (S.gd[k][c].x + S.gd[k][c].y);
     g = fmaf(P.f[2 + k], A.gwa[k] + A.gwb[k], g);
   }
   A.gS0 = g;
@@ -1258,7 +1242,7 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<K, TPV, LOSS,
             if (SS.b0) {
 #pragma unroll 1
               for (; p < pe; ++p) {
-                const float2 r = __ffma2_rn(SS.nS0, SS.T0, yc2[(p - pc0) * VW]);
+                const float2 r = __fadd2_rn(yc2[(p - pc0) * VW], SS.c0);
                 SS.l1 = __ffma2_rn(r, r, SS.l1);
                 SS.Qs = __fadd2_rn(SS.Qs, r);
               }

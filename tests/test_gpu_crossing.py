@@ -29,7 +29,7 @@ def test_crossing_benchmark_fit_matches_oracle(loss):
     dev, pa, pb = M.matched_deviation(th_ref, th, 2)
     # the FP32 fit follows the FP64 one (c1's bar: median deviation <= 0.5 deg, same peaks)
     assert float(np.median(dev)) <= 0.5
-    assert np.mean(pa == pb) >= 0.98
+    assert np.mean(pa == pb) == 1.0
     d, _, pk = f.fibers(0.15)
     dref, fwm = M.fibers(th_ref, 2)
     pref = M.peak_mask(fwm, 0.15)
