@@ -55,9 +55,9 @@ FLOPS_PER_B0_PAIR_SHELL = 4
 # DRAM bytes per voxel-iteration of the fused kernel (read + write) from an ncu capture of the
 # scaled brain (traffic grows in proportion to the voxels), valid only for the kernel sources
 # whose SHA-256 is TRAFFIC_SOURCES_SHA256: any other hash reports the traffic as null.
-# 212,900 voxels: 385.2 and 384.5 MB in two launches (profiles/k_iter_fused_hcp_brain_dram_traffic.md).
-TRAFFIC_BYTES_PER_VOXEL_ITER = 1807.7
-TRAFFIC_SOURCES_SHA256 = "65ed460f8bb1e30ee76a0cdbad15885be032b8ac256eae1a746dabd1213ab99b"
+# 212,900 voxels: 384.5 and 384.4 MB in two launches (profiles/k_iter_fused_hcp_brain_dram_traffic.md).
+TRAFFIC_BYTES_PER_VOXEL_ITER = 1805.7
+TRAFFIC_SOURCES_SHA256 = "50a3126af1645c74c4edbc527daa8bda483f3f900ddad7a6f04276feb4ffa35f"
 FUSED_SOURCES = ("prism_kernels.cuh", "prism_device.cuh", "prism_kset.cuh", "bessel_fit.h", "prism_k3.cu")
 # FP32 lanes per SM on GB300 (4 sub-partitions x 32); the peak multiplies them by the device's
 # SM count, 2 flops per fused multiply-add and the maximum SM clock seen by nvidia-smi.

@@ -1247,8 +1247,9 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<K, TPV, LOSS,
                 SS.Qs = __fadd2_rn(SS.Qs, r);
               }
             } else {
-              // four steps in flight (2 % faster than two on the brain workload; no spills)
-#pragma unroll 4
+              // three steps in flight (on the brain workload unroll 2 / 4 / 8 measured 0.1-0.3 %
+              // slower, 6 2.5 % slower; no spills in any)
+#pragma unroll 3
               for (; p < pe; ++p) {
                 const float4 gq = gxy[p];
                 shell_step(SS, make_float2(gq.x, gq.y), make_float2(gq.z, gq.w), gz2[p], yc2[(p - pc0) * VW]);
