@@ -18,6 +18,7 @@
 #include <utility>
 #include <vector>
 
+#include "host_pool.h"
 #include "prism.h"
 #include "prism_kernels.cuh"
 #include "prism_launch.h"
@@ -457,20 +458,16 @@ static bool shell_runs(const prism_volume& v, const int32_t* ord, std::vector<Sh
   return ok && nr <= kMaxRuns;
 }
 
-// Runs fn(begin, end) over [0, n) split into contiguous chunks on up to 16 host threads (one
-// chunk, on the calling thread, below `min_per_thread` items per thread).
+// Runs fn(begin, end) over [0, n) split into contiguous chunks on the process's host worker
+// pool (up to 16 threads with the caller; one chunk, on the calling thread, below
+// `min_per_thread` items per thread, or when the pool is busy or absent).
 template <typename F>
 static void parallel_chunks(int64_t n, int64_t min_per_thread, F fn) {
-  unsigned hc = std::thread::hardware_concurrency();
-  int64_t nt = std::min<int64_t>(hc ? hc : 1, 16);
+  HostPool* pool = HostPool::get();
+  int64_t nt = pool ? pool->threads() : 1;
   nt = std::max<int64_t>(1, std::min<int64_t>(nt, n / std::max<int64_t>(min_per_thread, 1)));
-  if (nt <= 1) {
-    fn(int64_t{0}, n);
-    return;
-  }
-  std::vector<std::thread> th;
-  for (int64_t i = 0; i < nt; ++i) th.emplace_back(fn, n * i / nt, n * (i + 1) / nt);
-  for (auto& t : th) t.join();
+  if (nt > 1 && pool->run(n, static_cast<int>(nt), HostPool::Fn(fn))) return;
+  fn(int64_t{0}, n);
 }
 
 // Order in which the fused kernel's queue hands out tiles: every full tile in plan order
@@ -1608,44 +1605,83 @@ extern "C" int prism_fit_init_slabs(const prism_volume* vol, int32_t slab, int32
     if (z1s.back() >= nz) break;
   }
   const int S = static_cast<int>(z0s.size());
-  // whole-volume mask order (C order) -> per-slab mask order (the same relative order)
+  // the slabs holding each slice: za[z] always, zb[z] = za[z] + 1 in an overlap (else -1); with
+  // stride slab - overlap >= overlap no slice lies in three slabs
+  std::vector<int32_t> za(nz, -1), zb(nz, -1);
+  for (int s = 0; s < S; ++s)
+    for (int z = z0s[s]; z < z1s[s]; ++z) {
+      if (zb[z] >= 0) return fail(PRISM_E_INVALID_ARG, "a slice lies in three slabs");
+      (za[z] < 0 ? za[z] : zb[z]) = s;
+    }
+  // whole-volume mask order (C order) -> per-slab mask order (the same relative order), in two
+  // passes over chunks of x (counts, then the entries at the chunks' offsets)
   std::vector<std::vector<int64_t>> rows(S);
   std::vector<std::vector<uint8_t>> sub(S);
   for (int s = 0; s < S; ++s) sub[s].assign(static_cast<size_t>(nx) * ny * (z1s[s] - z0s[s]), 0);
-  std::vector<int64_t> src0, src1;
-  std::vector<int32_t> slab0, slab1;
-  std::vector<float> w1;
-  int64_t v = 0;
-  for (int x = 0; x < nx; ++x)
-    for (int y = 0; y < ny; ++y)
-      for (int z = 0; z < nz; ++z) {
-        if (!vol->mask[(static_cast<int64_t>(x) * ny + y) * nz + z]) continue;
-        int first = -1;
-        int64_t i0 = -1, i1 = -1;
-        float wt = 0.f;
-        for (int s = 0; s < S; ++s) {
-          if (z < z0s[s] || z >= z1s[s]) continue;
-          const int zl = z - z0s[s];
-          sub[s][(static_cast<size_t>(x) * ny + y) * (z1s[s] - z0s[s]) + zl] = 1;
-          const int64_t idx = static_cast<int64_t>(rows[s].size());
-          rows[s].push_back(v);
-          if (first < 0) {
-            first = s;
-            i0 = idx;
-          } else {
-            i1 = idx;
-            // linear ramp across the overlap of slabs first and s
-            wt = (static_cast<float>(z - z0s[s]) + 0.5f) / static_cast<float>(z1s[first] - z0s[s]);
+  const int nxc = std::min(nx, 64);
+  std::vector<int64_t> cnt(static_cast<size_t>(nxc + 1) * (S + 1), 0);   // [chunk + 1][S + 1]
+  auto xr = [&](int c, int& xa, int& xe) {
+    xa = static_cast<int>(static_cast<int64_t>(nx) * c / nxc);
+    xe = static_cast<int>(static_cast<int64_t>(nx) * (c + 1) / nxc);
+  };
+  parallel_chunks(nxc, 1, [&](int64_t cb, int64_t ce) {
+    for (int c = static_cast<int>(cb); c < ce; ++c) {
+      int xa, xe;
+      xr(c, xa, xe);
+      int64_t* k = cnt.data() + static_cast<size_t>(c + 1) * (S + 1);
+      for (int x = xa; x < xe; ++x)
+        for (int y = 0; y < ny; ++y) {
+          const uint8_t* m = vol->mask + (static_cast<int64_t>(x) * ny + y) * nz;
+          for (int z = 0; z < nz; ++z)
+            if (m[z]) {
+              ++k[S];
+              ++k[za[z]];
+              if (zb[z] >= 0) ++k[zb[z]];
+            }
+        }
+    }
+  });
+  for (int c = 0; c < nxc; ++c)
+    for (int s = 0; s <= S; ++s) cnt[static_cast<size_t>(c + 1) * (S + 1) + s] += cnt[static_cast<size_t>(c) * (S + 1) + s];
+  const int64_t V = cnt[static_cast<size_t>(nxc) * (S + 1) + S];
+  for (int s = 0; s < S; ++s) rows[s].resize(static_cast<size_t>(cnt[static_cast<size_t>(nxc) * (S + 1) + s]));
+  std::vector<int64_t> src0(V), src1(V);
+  std::vector<int32_t> slab0(V), slab1(V);
+  std::vector<float> w1(V);
+  parallel_chunks(nxc, 1, [&](int64_t cb, int64_t ce) {
+    std::vector<int64_t> at(S + 1);
+    for (int c = static_cast<int>(cb); c < ce; ++c) {
+      int xa, xe;
+      xr(c, xa, xe);
+      for (int s = 0; s <= S; ++s) at[s] = cnt[static_cast<size_t>(c) * (S + 1) + s];
+      for (int x = xa; x < xe; ++x)
+        for (int y = 0; y < ny; ++y) {
+          const uint8_t* m = vol->mask + (static_cast<int64_t>(x) * ny + y) * nz;
+          for (int z = 0; z < nz; ++z) {
+            if (!m[z]) continue;
+            const int64_t v = at[S]++;
+            const int first = za[z], second = zb[z];
+            const int64_t i0 = at[first]++;
+            rows[first][i0] = v;
+            sub[first][(static_cast<size_t>(x) * ny + y) * (z1s[first] - z0s[first]) + (z - z0s[first])] = 1;
+            int64_t i1 = -1;
+            float wt = 0.f;
+            if (second >= 0) {
+              i1 = at[second]++;
+              rows[second][i1] = v;
+              sub[second][(static_cast<size_t>(x) * ny + y) * (z1s[second] - z0s[second]) + (z - z0s[second])] = 1;
+              // linear ramp across the overlap of slabs first and second
+              wt = (static_cast<float>(z - z0s[second]) + 0.5f) / static_cast<float>(z1s[first] - z0s[second]);
+            }
+            slab0[v] = first;
+            src0[v] = i0;
+            slab1[v] = second;
+            src1[v] = i1;
+            w1[v] = wt;
           }
         }
-        slab0.push_back(first);
-        src0.push_back(i0);
-        slab1.push_back(i1 >= 0 ? first + 1 : -1);
-        src1.push_back(i1);
-        w1.push_back(wt);
-        ++v;
-      }
-  const int64_t V = v;
+    }
+  });
   if (V == 0) return fail(PRISM_E_SHAPE, "the mask is empty");
   // non-empty slabs become the handle's volumes; handle voxel = vox0[g] + index in the slab
   std::vector<int> gidx(S, -1);
@@ -1658,10 +1694,12 @@ extern "C" int prism_fit_init_slabs(const prism_volume* vol, int32_t slab, int32
       vox0.push_back(acc);
       acc += static_cast<int64_t>(rows[s].size());
     }
-  for (int64_t i = 0; i < V; ++i) {
-    src0[i] += vox0[gidx[slab0[i]]];
-    if (src1[i] >= 0) src1[i] += vox0[gidx[slab1[i]]];
-  }
+  parallel_chunks(V, 1 << 15, [&](int64_t b, int64_t e) {
+    for (int64_t i = b; i < e; ++i) {
+      src0[i] += vox0[gidx[slab0[i]]];
+      if (src1[i] >= 0) src1[i] += vox0[gidx[slab1[i]]];
+    }
+  });
   // whole-volume signal (and initial parameters) on the device, then one gathered copy per slab
   DevTmp dsig, dinit, drows;
   const float* sig = vol->signal;

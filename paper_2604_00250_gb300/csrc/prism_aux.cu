@@ -11,30 +11,44 @@ namespace prism {
 // ---------------------------------------------------------------------------
 // Preprocessing (Sec. 2.5: both y and y_hat are divided by the measured b0).
 // ---------------------------------------------------------------------------
-__global__ void k_b0_stats(const float* __restrict__ sig, int64_t V, int N, const uint8_t* __restrict__ isb0,
-                           int nb0, float* __restrict__ b0mean, double* __restrict__ part, int* bad) {
+// One warp per voxel (the lanes read the row's consecutive measurements together), 256 voxels
+// per block of 256 threads; part[block] is the block's sum of the squared b0 deviations. The
+// per-voxel sums are FP32 (a b0 mean of a few dozen positive values, stored as FP32); the
+// squared deviations accumulate in FP64 per thread and per block.
+__global__ void __launch_bounds__(256) k_b0_stats(const float* __restrict__ sig, int64_t V, int N,
+                                                  const uint8_t* __restrict__ isb0, int nb0,
+                                                  float* __restrict__ b0mean, double* __restrict__ part, int* bad) {
   __shared__ double s[256];
-  const int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  __shared__ uint8_t s_b0[1024];   // N <= 1024 (prism_fit_init checks it)
+  for (int n = threadIdx.x; n < N; n += blockDim.x) s_b0[n] = isb0[n];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double acc = 0.0;
-  if (v < V) {
+  for (int j = 0; j < 32; ++j) {
+    const int64_t v = static_cast<int64_t>(blockIdx.x) * 256 + warp * 32 + j;
+    if (v >= V) break;
     const float* row = sig + v * N;
-    double m = 0.0;
+    float m = 0.f;
     bool finite = true;
-    for (int n = 0; n < N; ++n) {
+    for (int n = lane; n < N; n += 32) {
       const float x = row[n];
       if (!isfinite(x)) finite = false;
-      if (isb0[n]) m += x;
+      if (s_b0[n]) m += x;
     }
-    m /= nb0;
-    if (!finite || !(m > 0.0)) {
-      atomicAdd(bad, 1);
-      m = 1.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
+    finite = __all_sync(0xffffffffu, finite);
+    m /= static_cast<float>(nb0);
+    if (!finite || !(m > 0.f)) {
+      if (lane == 0) atomicAdd(bad, 1);
+      m = 1.f;
     }
-    b0mean[v] = static_cast<float>(m);
-    for (int n = 0; n < N; ++n)
-      if (isb0[n]) {
-        const double d = row[n] / m - 1.0;
-        acc += d * d;
+    if (lane == 0) b0mean[v] = m;
+    const float inv = 1.f / m;
+    for (int n = lane; n < N; n += 32)
+      if (s_b0[n]) {
+        const float d = fmaf(row[n], inv, -1.f);
+        acc += static_cast<double>(d * d);
       }
   }
   s[threadIdx.x] = acc;
@@ -58,20 +72,53 @@ __global__ void k_sigma_init(const double* part, int nblocks, int64_t V, int nb0
   *sigma_log = static_cast<float>(log(sg));
 }
 
-__global__ void k_pack(const IterArgs a, const float* __restrict__ sig, const float* __restrict__ b0mean,
-                       const int32_t* __restrict__ vox_of_slot, const int32_t* __restrict__ order, int64_t vox0,
-                       int tile_begin, int N, float* __restrict__ ypack) {
+// One tile per block of kPackThreads: each warp column of the tile (VW voxels) in chunks of
+// kPackC measurements, staged in shared memory so that the reads run along the voxels' signal
+// rows and the writes along the packed [pair][voxel][2] layout (ypos).
+constexpr int kPackThreads = 256, kPackC = 128;
+template <int VW>
+__global__ void __launch_bounds__(kPackThreads) k_pack(const IterArgs a, const float* __restrict__ sig,
+                                                       const float* __restrict__ b0mean,
+                                                       const int32_t* __restrict__ vox_of_slot,
+                                                       const int32_t* __restrict__ order, int64_t vox0, int tile_begin,
+                                                       int N, float* __restrict__ ypack) {
+  __shared__ float s[VW][kPackC + 1];
+  __shared__ int64_t s_row[VW];   // the voxel's signal row (-1: padding slot)
+  __shared__ float s_inv[VW];     // 1 / its b0 mean
   const int t = tile_begin + blockIdx.x;
   const Tile tl = a.tiles[t];
   const int NP = (N + 3) & ~3;
-  for (int e = threadIdx.x; e < NP * a.TV; e += blockDim.x) {
-    const int n = e / a.TV, vl = e - n * a.TV;
-    float val = 0.f;
-    if (vl < tl.count && n < N) {
-      const int64_t v = vox_of_slot[tl.slot0 + vl] - vox0;
-      val = sig[v * N + order[n]] / b0mean[v];
+  for (int w = 0; w * VW < a.TV; ++w) {
+    if (threadIdx.x < VW) {
+      const int vl = w * VW + threadIdx.x;
+      int64_t r = -1;
+      float inv = 0.f;
+      if (vl < tl.count) {
+        const int64_t v = vox_of_slot[tl.slot0 + vl] - vox0;
+        r = v * N;
+        inv = 1.f / b0mean[v];
+      }
+      s_row[threadIdx.x] = r;
+      s_inv[threadIdx.x] = inv;
     }
-    ypack[ypos(tl, n, vl, a.VW)] = val;
+    __syncthreads();
+    for (int n0 = 0; n0 < NP; n0 += kPackC) {
+      const int C = min(kPackC, NP - n0);   // even (NP and kPackC are multiples of 4)
+#pragma unroll 8
+      for (int i = threadIdx.x; i < VW * C; i += kPackThreads) {
+        const int j = i / C, nc = i - j * C, n = n0 + nc;
+        const int64_t r = s_row[j];
+        s[j][nc] = (r >= 0 && n < N) ? sig[r + order[n]] * s_inv[j] : 0.f;
+      }
+      __syncthreads();
+      float* out = ypack + tl.y_off + static_cast<size_t>(w) * NP * VW + static_cast<size_t>(n0) * VW;
+#pragma unroll 8
+      for (int i = threadIdx.x; i < VW * C; i += kPackThreads) {
+        const int pc = i / (2 * VW), r = i - pc * 2 * VW, j = r >> 1;
+        out[i] = s[j][2 * pc + (r & 1)];
+      }
+      __syncthreads();
+    }
   }
 }
 
@@ -209,7 +256,9 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
   x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
   return x ^ (x >> 31);
 }
-__device__ __forceinline__ double u01(uint64_t h) { return ((h >> 11) + 0.5) * (1.0 / 9007199254740992.0); }
+__device__ __forceinline__ float u01f(uint64_t h) {
+  return (static_cast<float>(h >> 40) + 0.5f) * (1.f / 16777216.f);   // 24 bits, in (0, 1)
+}
 
 // Default start: S0 = 1, equal fractions, f_intra = 0.5, directions uniform on the sphere,
 // drawn per grid position (so that a voxel starts from the same values whichever of the
@@ -222,19 +271,23 @@ __global__ void k_default_init(const int32_t* __restrict__ slot_of_vox, const ui
   int cx, cy, cz;
   unpack_coord(vcoord[slot], cx, cy, cz);
   const int64_t v = (static_cast<int64_t>(cx) * ny + cy) * nz + cz;
-  theta[slot] = static_cast<float>(log(exp(1.0) - 1.0));
+  theta[slot] = 0.5413248546129181f;   // log(e - 1): S0 = softplus(raw) = 1
   for (int i = 0; i < K + 3; ++i) theta[static_cast<size_t>(1 + i) * Vpad + slot] = 0.f;
   for (int k = 0; k < K; ++k) {
-    double g[3];
+    // normalised Gaussian triple by the Box-Muller transform, in FP32 (u1 >= 2^-25 keeps the
+    // radius above 2e-4, so the norm is never 0)
+    float g[3];
     for (int c = 0; c < 3; c += 2) {
       const uint64_t base = seed * 0x100000001B3ull ^ (static_cast<uint64_t>(v) << 8) ^ (k * 4 + c);
-      const double u1 = u01(splitmix64(base)), u2 = u01(splitmix64(base ^ 0xABCDEF12345ull));
-      const double rad = sqrt(-2.0 * log(u1));
-      g[c] = rad * cos(6.283185307179586 * u2);
-      if (c + 1 < 3) g[c + 1] = rad * sin(6.283185307179586 * u2);
+      const float u1 = u01f(splitmix64(base)), u2 = u01f(splitmix64(base ^ 0xABCDEF12345ull));
+      const float rad = sqrtf(-2.f * logf(u1));
+      float sn, cs;
+      sincospif(2.f * u2, &sn, &cs);
+      g[c] = rad * cs;
+      if (c + 1 < 3) g[c + 1] = rad * sn;
     }
-    const double nr = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]) + 1e-300;
-    for (int c = 0; c < 3; ++c) theta[static_cast<size_t>(K + 4 + 3 * k + c) * Vpad + slot] = static_cast<float>(g[c] / nr);
+    const float inv = rsqrtf(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    for (int c = 0; c < 3; ++c) theta[static_cast<size_t>(K + 4 + 3 * k + c) * Vpad + slot] = g[c] * inv;
   }
   theta[static_cast<size_t>(4 * K + 4) * Vpad + slot] = 0.f;
 }
@@ -632,7 +685,14 @@ cudaError_t launch_pack(const IterArgs& a, const float* sig, const float* b0mean
                         int* bad, cudaStream_t st) {
   (void)bad;
   if (tile_end <= tile_begin) return cudaSuccess;
-  k_pack<<<tile_end - tile_begin, 256, 0, st>>>(a, sig, b0mean, vox_of_slot, order, vox0, tile_begin, N, ypack);
+  if (a.TV % a.VW != 0) return cudaErrorInvalidValue;
+  const int nb = tile_end - tile_begin;
+  switch (a.VW) {
+    case 32: k_pack<32><<<nb, kPackThreads, 0, st>>>(a, sig, b0mean, vox_of_slot, order, vox0, tile_begin, N, ypack); break;
+    case 8: k_pack<8><<<nb, kPackThreads, 0, st>>>(a, sig, b0mean, vox_of_slot, order, vox0, tile_begin, N, ypack); break;
+    case 2: k_pack<2><<<nb, kPackThreads, 0, st>>>(a, sig, b0mean, vox_of_slot, order, vox0, tile_begin, N, ypack); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 cudaError_t launch_slot_data(const Tile* tiles, const GroupDev* groups, int G, const GroupDev* host_groups,

@@ -23,6 +23,7 @@ import phantoms as P
 from oracle import prism_oracle as O
 from tests.helpers import (TOL_GRAD, TOL_LOSS, TOL_SIGNAL, block_slices, make_pair, normwise, oracle_opts,
                            signal_rel, split_groups)
+from tests.test_gpu_fused_gradient import fused_gradient
 
 pytestmark = pytest.mark.gpu
 
@@ -183,8 +184,11 @@ def test_disco_shaped_configuration_sampled_patches():
     """The DiSCo1-shaped fit of bench.py --workload disco (40^3, N = 364 up to b = 13,192, K = 5,
     Rician NLL, topology and smoothness priors) in its default launch configuration (on a GB300
     four lanes per voxel: 500 tiles of 128 voxels would fill 456 resident CTAs 1.1 times), one
-    graph-replayed iteration: the parameters of sampled whole patches against the oracle's Adam
-    step from the same start and group parameters."""
+    graph-replayed iteration from the default start: the gradient of sampled whole patches (read
+    from Adam's first moment, m = (1 - beta1) g after one step) against the oracle's, normwise
+    per parameter block. (Comparing the stepped parameters instead would test rounding noise:
+    Adam's first step turns every gradient component above eps into +-lr, among them the radial
+    components of the raw directions, which are zero up to rounding.)"""
     sch = P.make_scheme(4, [(1000, 90), (3000, 90), (7000, 90), (13192, 90)], 0)
     vol = P.bundle_phantom(0, edge=40, snr=50.0, scheme=sch, device="cuda")
     K = 5
@@ -202,17 +206,15 @@ def test_disco_shaped_configuration_sampled_patches():
     gp = split_groups(f.groups().copy(), f)[0]
     f.step(1)
     f.sync()
-    th1 = f.params_host()
+    g_vox, _ = fused_gradient(f, f.opts.beta1)
     f.close()
     ids, _ = _patch_ids(vol, 16, 4)
     ov = O.OracleVolume(vol.mask, vol.signal, vol.bvals, vol.bvecs, oracle_opts(**kw), patches=ids)
     th = torch.as_tensor(th0[ov.sel]).double()
-    adam = O.Adam(ov.opts)
-    adam.t += 1
     _, _, g, _ = O.value_and_grad(ov, th, gp, n_norm=ov.n_mask)
-    ref = adam.step("theta", th, g).numpy()
-    diff = np.abs(th1[ov.sel] - ref)
-    assert float(diff.max()) < 3e-4, float(diff.max())
+    for name, sl in block_slices(K).items():
+        e = normwise(g_vox[ov.sel][:, sl], g[:, sl].numpy())
+        assert e <= TOL_GRAD, (name, e)
 
 
 def test_mixed_batch_full():
