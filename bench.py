@@ -55,9 +55,9 @@ FLOPS_PER_B0_PAIR_SHELL = 4
 # DRAM bytes per voxel-iteration of the fused kernel (read + write) from an ncu capture of the
 # scaled brain (traffic grows in proportion to the voxels), valid only for the kernel sources
 # whose SHA-256 is TRAFFIC_SOURCES_SHA256: any other hash reports the traffic as null.
-# 212,900 voxels: 384.5 and 384.4 MB in two launches (profiles/k_iter_fused_hcp_brain_dram_traffic.md).
-TRAFFIC_BYTES_PER_VOXEL_ITER = 1805.7
-TRAFFIC_SOURCES_SHA256 = "50a3126af1645c74c4edbc527daa8bda483f3f900ddad7a6f04276feb4ffa35f"
+# 212,900 voxels: 384.6 and 383.9 MB in two launches (profiles/k_iter_fused_hcp_brain_dram_traffic.md).
+TRAFFIC_BYTES_PER_VOXEL_ITER = 1804.6
+TRAFFIC_SOURCES_SHA256 = "bebce4bfbb6e8b7ae9e2ea602aff22b9132dfec4f127d72954d37ebf938b0a45"
 FUSED_SOURCES = ("prism_kernels.cuh", "prism_device.cuh", "prism_kset.cuh", "bessel_fit.h", "prism_k3.cu")
 # FP32 lanes per SM on GB300 (4 sub-partitions x 32); the peak multiplies them by the device's
 # SM count, 2 flops per fused multiply-add and the maximum SM clock seen by nvidia-smi.

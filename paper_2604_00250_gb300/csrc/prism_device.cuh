@@ -59,6 +59,12 @@ struct __align__(16) ShellRun {
 constexpr int kMaxRuns = 16;        // shells per group the shell loop takes
 constexpr int kShellCols = 10;      // per-thread shared-memory column of the shell loop (floats)
 constexpr float kRho = 1.f - 0.4f / 1.7f;   // 1 - D_perp / D_par (Eq. 5)
+
+// Programmatic dependent launch: wait until the grids this one depends on have completed and
+// their writes are visible (a no-op for a grid launched without the programmatic attribute),
+// and let the dependent grid start launching.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 constexpr float kTwoLn2 = 1.3862943611198906f;   // 2 ln 2: d(2^(-x^2))/dx = -2 ln 2 x 2^(-x^2)
 
 // A tile: up to TV voxels of one patch, processed by one CTA.
@@ -127,7 +133,11 @@ struct IterArgs {
   float lam_orphan, inv_s_orphan, lam_order;
   // Group finalisation done by the fused kernel's last CTA when no group has calibration:
   // objective per group, its history, Adam on sigma_log (NLL), step counter.
-  int32_t fold_groups, loss_mode, hist_len, pad_;
+  int32_t fold_groups, loss_mode, hist_len;
+  // Host side: launch the iteration's neighbour-prior kernels and the fused kernel after them as
+  // programmatic dependents (each starts while its predecessor finishes and waits on the device,
+  // griddepcontrol, before it reads what the predecessor writes).
+  int32_t pdl;
   float* gparams_rw;       // same array as gparams
   float* gm;               // group Adam moments (packed like gparams)
   float* gv;

@@ -1087,6 +1087,10 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<K, TPV, LOSS,
   uint32_t base = 0;   // stream position of the current tile's chunk 0
   bool failed = false;
   int t = s_first;
+  // launched as a programmatic dependent of k_prior_grad, this grid can start while that one
+  // finishes: its rows are read only in the epilogue, so each thread waits once, before its
+  // first epilogue (no write before that point is read by k_prior_grad)
+  bool dep_done = false;
 
   // Lane 0: issue stream position `pos` = chunk j of the tile at y_off (NP padded rows).
   auto issue = [&](uint32_t pos, int64_t y_off, int NP, int j) {
@@ -1417,6 +1421,10 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<K, TPV, LOSS,
       acc_reduce_tpv<K, TPV, VW>(A);
       if (js == 0) acc_put<K>(A, s_acc, TV, vl);
       __syncthreads();
+    }
+    if (!dep_done) {
+      grid_dep_wait();
+      dep_done = true;
     }
     // the epilogue's voxel: the thread's own with one thread per voxel, else voxel tid of the
     // tile for the first TV threads (the others skip to the tile partials)
@@ -1850,6 +1858,10 @@ __global__ void __launch_bounds__(256) k_adjoint(const IterArgs a, const PlainAr
 template <int K>
 __global__ void k_prior_prep(const IterArgs a, int tile_begin, int tile_end) {
   constexpr int NF = K + 3, XF = 4 * K + 3;
+  // launched as a programmatic dependent of the previous iteration's fused kernel: wait for it
+  // before any read, then let k_prior_grad start launching
+  grid_dep_wait();
+  grid_dep_launch();
   const int slot = tile_begin * a.TV + blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= tile_end * a.TV) return;
   const Tile tl = a.tiles[slot / a.TV];
@@ -1908,6 +1920,10 @@ __global__ void k_prior_prep(const IterArgs a, int tile_begin, int tile_end) {
 template <int K>
 __global__ void k_prior_grad(const IterArgs a, int tile_begin, int tile_end) {
   constexpr int NF = K + 3, XF = 4 * K + 3;
+  // as k_prior_prep: wait for the predecessor, then let the fused kernel start launching (its
+  // prologue and loop read nothing this kernel writes; it waits before its first epilogue)
+  grid_dep_wait();
+  grid_dep_launch();
   const int slot = tile_begin * a.TV + blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= tile_end * a.TV) return;
   const Tile tl = a.tiles[slot / a.TV];
