@@ -54,10 +54,11 @@ FLOPS_PER_B0_PAIR = 5
 FLOPS_PER_B0_PAIR_SHELL = 4
 # DRAM bytes per voxel-iteration of the fused kernel (read + write) from an ncu capture of the
 # scaled brain (traffic grows in proportion to the voxels), valid only for the kernel sources
-# whose SHA-256 is TRAFFIC_SOURCES_SHA256: any other hash reports the traffic as null.
+# whose SHA-256 (comments and blank lines left out, fused_sources_sha256) is
+# TRAFFIC_SOURCES_SHA256: any other hash reports the traffic as null.
 # 212,900 voxels: 384.6 and 383.9 MB in two launches (profiles/k_iter_fused_hcp_brain_dram_traffic.md).
 TRAFFIC_BYTES_PER_VOXEL_ITER = 1804.6
-TRAFFIC_SOURCES_SHA256 = "bebce4bfbb6e8b7ae9e2ea602aff22b9132dfec4f127d72954d37ebf938b0a45"
+TRAFFIC_SOURCES_SHA256 = "6cd1f0b4f09f4bd86bb8c3b2df200f8fcf27136935bb43150bce09c5656b0537"
 FUSED_SOURCES = ("prism_kernels.cuh", "prism_device.cuh", "prism_kset.cuh", "bessel_fit.h", "prism_k3.cu")
 # FP32 lanes per SM on GB300 (4 sub-partitions x 32); the peak multiplies them by the device's
 # SM count, 2 flops per fused multiply-add and the maximum SM clock seen by nvidia-smi.
@@ -155,12 +156,38 @@ def speed_leg(vols, kw, steps, warmup, unfused_steps=2):
     return out
 
 
+def strip_c_comments(src):
+    """C/C++ source without its comments and blank lines (string and character literals kept
+    whole), so that a change of comments alone leaves the fused-kernel hash as it was."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    lines = (ln.rstrip() for ln in "".join(out).split("\n"))
+    return "\n".join(ln for ln in lines if ln)
+
+
 def fused_sources_sha256():
+    """SHA-256 of the fused kernel's sources, comments and blank lines left out."""
     import hashlib
     h = hashlib.sha256()
     for name in FUSED_SOURCES:
-        with open(os.path.join(ROOT, "paper_2604_00250_gb300", "csrc", name), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2604_00250_gb300", "csrc", name), encoding="utf-8") as fh:
+            h.update(strip_c_comments(fh.read()).encode("utf-8"))
     return h.hexdigest()
 
 

@@ -820,7 +820,8 @@ __device__ __forceinline__ void shell_close(ShellState<K>& S, const ShellRun& R,
   S.Qs = make_float2(0.f, 0.f);
 }
 
-// Opens shell R: its isotropic mixture, exponent offset, derivative constants and s d_k.
+// Opens shell R: the residual's constant -S0 T0 (T0 the shell's isotropic mixture, at b = 0 the
+// sum of every fraction) and the exponent offset Kp.
 template <int K>
 __device__ __forceinline__ void shell_open(ShellState<K>& S, const ShellRun& R, const float* col) {
   using SR = ShellRows<K>;
