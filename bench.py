@@ -635,13 +635,17 @@ def run_slabs(args):
     opts = prism.options(K=K_FIB, loss="mse", patch_dim=16, lam_orphan=0.01, lam_order=0.01, optimizer="rprop",
                          **PRIORS)
     iters = 100
+    # the stitched maps go into pinned host arrays allocated once, like the input signal
+    V_all = vol.n_vox
+    outs = tuple(torch.empty(s, dtype=torch.float32, pin_memory=True)
+                 for s in ((V_all,), (V_all, K_FIB + 3), (V_all,), (V_all, K_FIB, 3)))
     times = []
     for rep in range(2):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         f = prism.Fitter(vh, opts, slabs=(30, 5))
         f.step(iters)
-        s0, fr, fin, d = f.stitch()
+        s0, fr, fin, d = f.stitch(out=outs)
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
         n_slab_vox, n_slabs = f.n_vox, f.n_groups

@@ -213,17 +213,19 @@ class Fitter:
                                               _stream_ptr(stream)))
         torch.cuda.current_stream().synchronize()
 
-    def stitch(self):
+    def stitch(self, out=None):
         """Whole-volume maps of a slab fit: (S0 [V], fractions [V, K+3], f_intra [V],
-        unit directions [V, K, 3]) in the volume's mask order, numpy float32."""
+        unit directions [V, K, 3]) in the volume's mask order, float32. By default new numpy
+        arrays; `out` = four arrays of those shapes to write into instead (numpy arrays, or torch
+        tensors all on the host or all on the GPU, C-contiguous float32), for example pinned host
+        tensors kept across fits, which spares the first touch of fresh host pages."""
         V, K = self.n_out, self.K
-        s0 = np.empty(V, np.float32)
-        fr = np.empty((V, K + 3), np.float32)
-        fi = np.empty(V, np.float32)
-        d = np.empty((V, K, 3), np.float32)
-        _lib.check(self._lib.prism_stitch_slabs(self._h, s0.ctypes.data, fr.ctypes.data, fi.ctypes.data,
-                                                d.ctypes.data, MEM_HOST, _stream_ptr(None)))
-        return s0, fr, fi, d
+        shapes = ((V,), (V, K + 3), (V,), (V, K, 3))
+        if out is None:
+            out = tuple(np.empty(s, np.float32) for s in shapes)
+        ptrs, mem = _out_pointers(out, shapes)
+        _lib.check(self._lib.prism_stitch_slabs(self._h, *ptrs, mem, _stream_ptr(None)))
+        return tuple(out)
 
     def fibers(self, rel_thresh=0.15):
         """(unit directions [V, K, 3], fractions [V, K+3], peak flags [V, K]) as numpy arrays."""
@@ -358,6 +360,31 @@ def fit(volumes, opts=None, n_iters=200, stream=None, **kw):
     _lib.check(lib.prism_fit(arr, n, ctypes.byref(o), int(n_iters), theta.ctypes.data, loss.ctypes.data, MEM_HOST,
                              _stream_ptr(stream)))
     return theta, loss
+
+
+def _out_pointers(arrays, shapes):
+    """Data pointers and memory space (MEM_HOST / MEM_DEVICE) of caller-provided output arrays,
+    each checked against its shape: numpy arrays, or torch tensors all on the host or all on the
+    GPU; C-contiguous float32."""
+    if len(arrays) != len(shapes):
+        raise ValueError(f"expected {len(shapes)} output arrays, got {len(arrays)}")
+    ptrs, spaces = [], set()
+    for a, shp in zip(arrays, shapes):
+        if isinstance(a, np.ndarray):
+            if a.dtype != np.float32 or not a.flags.c_contiguous or a.shape != tuple(shp):
+                raise ValueError(f"output array must be C-contiguous float32 of shape {tuple(shp)}")
+            ptrs.append(ctypes.c_void_p(a.ctypes.data))
+            spaces.add(MEM_HOST)
+        else:
+            torch = _torch()
+            if (not isinstance(a, torch.Tensor) or a.dtype != torch.float32 or not a.is_contiguous()
+                    or tuple(a.shape) != tuple(shp)):
+                raise ValueError(f"output tensor must be contiguous float32 of shape {tuple(shp)}")
+            ptrs.append(ctypes.c_void_p(a.data_ptr()))
+            spaces.add(MEM_DEVICE if a.is_cuda else MEM_HOST)
+    if len(spaces) != 1:
+        raise ValueError("output arrays must all be on the host or all on the GPU")
+    return ptrs, spaces.pop()
 
 
 def microbench(kind):

@@ -131,6 +131,31 @@ def test_slab_signal_in_device_memory_gives_the_same_fit():
     f2.close()
 
 
+def test_stitch_into_given_arrays():
+    """stitch(out=...) writes the same maps into caller arrays: numpy, pinned host tensors, or
+    CUDA tensors; mismatched shapes or mixed memory spaces are refused before any call."""
+    vol = _volume(4, shape=(4, 4, 13))
+    f = _fitter(vol, 6, 2)
+    f.step(3)
+    ref = f.stitch()
+    V = f.n_out
+    shapes = ((V,), (V, K + 3), (V,), (V, K, 3))
+    outs = [tuple(np.full(s, np.nan, np.float32) for s in shapes),
+            tuple(torch.full(s, float("nan"), pin_memory=True) for s in shapes),
+            tuple(torch.full(s, float("nan"), device="cuda") for s in shapes)]
+    for out in outs:
+        got = f.stitch(out=out)
+        assert all(g is o for g, o in zip(got, out))
+        for g, r in zip(got, ref):
+            g = g.cpu().numpy() if isinstance(g, torch.Tensor) else g
+            np.testing.assert_array_equal(g, r)
+    with pytest.raises(ValueError):
+        f.stitch(out=(np.empty((V + 1,), np.float32),) + outs[0][1:])
+    with pytest.raises(ValueError):
+        f.stitch(out=outs[0][:2] + outs[2][2:])
+    f.close()
+
+
 def test_stitch_on_a_plain_handle_is_a_state_error():
     import paper_2604_00250_gb300 as prism
     from paper_2604_00250_gb300._lib import PrismError
