@@ -56,9 +56,9 @@ FLOPS_PER_B0_PAIR_SHELL = 4
 # scaled brain (traffic grows in proportion to the voxels), valid only for the kernel sources
 # whose SHA-256 (comments and blank lines left out, fused_sources_sha256) is
 # TRAFFIC_SOURCES_SHA256: any other hash reports the traffic as null.
-# 212,900 voxels: 384.6 and 383.9 MB in two launches (profiles/k_iter_fused_hcp_brain_dram_traffic.md).
-TRAFFIC_BYTES_PER_VOXEL_ITER = 1804.6
-TRAFFIC_SOURCES_SHA256 = "6cd1f0b4f09f4bd86bb8c3b2df200f8fcf27136935bb43150bce09c5656b0537"
+# 212,900 voxels: 384.4 and 384.1 MB in two launches (profiles/k_iter_fused_hcp_brain_dram_traffic.md).
+TRAFFIC_BYTES_PER_VOXEL_ITER = 1804.7
+TRAFFIC_SOURCES_SHA256 = "da28403d796e239c782cce8c6b9ec39009e819adfb07ce51d095c30ec0152732"
 FUSED_SOURCES = ("prism_kernels.cuh", "prism_device.cuh", "prism_kset.cuh", "bessel_fit.h", "prism_k3.cu")
 # FP32 lanes per SM on GB300 (4 sub-partitions x 32); the peak multiplies them by the device's
 # SM count, 2 flops per fused multiply-add and the maximum SM clock seen by nvidia-smi.

@@ -44,6 +44,13 @@ def arr(name, vals):
     return f"__device__ __constant__ float {name}[{len(vals)}] = {{{body}}};"
 
 
+def arr2(name, xs, ys):
+    """Two tables interleaved as float2 {x_k, y_k}: the two Horner chains that share an argument
+    then run as one packed f32x2 chain."""
+    body = ", ".join(f"{{{float(x):.9e}f, {float(y):.9e}f}}" for x, y in zip(xs, ys))
+    return f"__device__ __constant__ float2 {name}[{len(xs)}] = {{{body}}};"
+
+
 def main():
     ca = fit(pa)
     cb = fit(pb)
@@ -58,6 +65,8 @@ def main():
     print(arr("k_bessel_pb", cb))
     print(arr("k_bessel_s0", s0))
     print(arr("k_bessel_s1", s1))
+    print(arr2("k_bessel_pba", cb, ca))
+    print(arr2("k_bessel_s01", s0, s1))
 
 
 if __name__ == "__main__":

@@ -267,31 +267,35 @@ __device__ __forceinline__ float huber_drho(float r, float dl) {
 }
 
 // Q(z) = 1 - I1(z)/I0(z) and L(z) = log(exp(-z) I0(z)) for z >= 0, float32.
-// Power series below PRISM_BESSEL_ZS, fitted smooth functions of ZS/z above.
+// Power series below PRISM_BESSEL_ZS, fitted smooth functions of ZS/z above. The two Horner
+// chains of each branch share their argument, so they run as one packed f32x2 chain over the
+// interleaved tables (each lane the same round-to-nearest multiply-add as the scalar chain; on
+// GB300 the DiSCo1-shaped NLL fit's fused kernel 9 % faster).
 template <bool WANT_L>
 __device__ __forceinline__ void bessel_QL(float z, float& Q, float& L) {
   if (z < PRISM_BESSEL_ZS) {
     const float t = 0.25f * z * z;
-    float i0 = k_bessel_s0[PRISM_BESSEL_NSER - 1];
-    float i1 = k_bessel_s1[PRISM_BESSEL_NSER - 1];
+    const float2 tt = make_float2(t, t);
+    float2 s = k_bessel_s01[PRISM_BESSEL_NSER - 1];
 #pragma unroll
-    for (int k = PRISM_BESSEL_NSER - 2; k >= 0; --k) {
-      i0 = fmaf(i0, t, k_bessel_s0[k]);
-      i1 = fmaf(i1, t, k_bessel_s1[k]);
-    }
+    for (int k = PRISM_BESSEL_NSER - 2; k >= 0; --k) s = __ffma2_rn(s, tt, k_bessel_s01[k]);
+    const float i0 = s.x, i1 = s.y;
     Q = 1.f - 0.5f * z * i1 * rcpf_(i0);   // i0 >= 1
     if (WANT_L) L = lg2f_(i0) * kLn2 - z;
   } else {
     const float x = PRISM_BESSEL_ZS * rcpf_(z);
-    float pb = k_bessel_pb[PRISM_BESSEL_DEG];
-#pragma unroll
-    for (int k = PRISM_BESSEL_DEG - 1; k >= 0; --k) pb = fmaf(pb, x, k_bessel_pb[k]);
-    Q = pb * x * (1.f / PRISM_BESSEL_ZS);
     if (WANT_L) {
-      float pa = k_bessel_pa[PRISM_BESSEL_DEG];
+      const float2 xx = make_float2(x, x);
+      float2 p = k_bessel_pba[PRISM_BESSEL_DEG];
 #pragma unroll
-      for (int k = PRISM_BESSEL_DEG - 1; k >= 0; --k) pa = fmaf(pa, x, k_bessel_pa[k]);
-      L = (lg2f_(pa) - 0.5f * lg2f_(z)) * kLn2 - kHalfLog2Pi;
+      for (int k = PRISM_BESSEL_DEG - 1; k >= 0; --k) p = __ffma2_rn(p, xx, k_bessel_pba[k]);
+      Q = p.x * x * (1.f / PRISM_BESSEL_ZS);
+      L = (lg2f_(p.y) - 0.5f * lg2f_(z)) * kLn2 - kHalfLog2Pi;
+    } else {
+      float pb = k_bessel_pb[PRISM_BESSEL_DEG];
+#pragma unroll
+      for (int k = PRISM_BESSEL_DEG - 1; k >= 0; --k) pb = fmaf(pb, x, k_bessel_pb[k]);
+      Q = pb * x * (1.f / PRISM_BESSEL_ZS);
     }
   }
 }
