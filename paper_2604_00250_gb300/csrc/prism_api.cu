@@ -966,12 +966,14 @@ int init_impl(prism_handle* h, const prism_volume* vols, int n_vols, const std::
   return PRISM_OK;
 }
 
-int choose_shape(const prism_options& o, int64_t V, int* tpv, int* nt) {
+int choose_shape(const prism_options& o, int64_t V, bool shell, int* tpv, int* nt) {
   // Measured on GB300 (bundle phantoms, K = 3 and 5, MSE and NLL): sixteen lanes per voxel
   // below 2,048 voxels, four below 32,768 (1.1-1.9x faster than one). Above, one thread per
   // voxel, except where its 128-voxel tiles come to about one wave of the SMs' resident CTAs
   // (0.75-1.25 waves: the last tiles then run nearly alone); four lanes then balance the SMs
-  // better (40^3: 7-19 % faster; calibrated, 14-19 %).
+  // better (40^3: 7-19 % faster; calibrated, 14-19 %). Where the shell loop applies (`shell`:
+  // it needs one thread per voxel) four lanes pay only above one wave: 40^3 (0.82 waves) 20 %
+  // slower than the shell loop, 45^3 (1.17 waves) 2 % faster, 47^3 (1.33 waves) 4 % slower.
   if (o.threads_per_voxel) {
     *tpv = o.threads_per_voxel;
   } else if (V < 2048) {
@@ -987,11 +989,32 @@ int choose_shape(const prism_options& o, int64_t V, int* tpv, int* nt) {
     // CTAs per SM of the one-thread-per-voxel kernel (3 for five fibers, NLL or calibration)
     const int occ = (o.K >= 5 || o.loss == PRISM_LOSS_NLL || o.calibration) ? 3 : 4;
     const double waves = static_cast<double>(V) / 128.0 / (static_cast<double>(sms) * occ);
-    *tpv = (waves > 0.75 && waves <= 1.25) ? 4 : 1;
+    *tpv = (waves > (shell ? 1.0 : 0.75) && waves <= 1.25) ? 4 : 1;
   }
   // the fused kernel is compiled for 128-thread CTAs (4 resident per SM)
   *nt = o.fused ? 128 : (o.cta_threads ? o.cta_threads : 128);
   return PRISM_OK;
+}
+
+// Whether the fused kernel would take the shell loop with one thread per voxel: MSE without
+// calibration, K <= 3, shells not switched off, and every volume's b-value shells (runs of
+// equal b in sorted order) of even length and at most kMaxRuns of them.
+bool shells_apply(const prism_volume* vols, int n, const prism_options& o) {
+  if (!o.fused || o.loss != PRISM_LOSS_MSE || o.calibration || o.K > 3 || o.shells != 0) return false;
+  for (int g = 0; g < n; ++g) {
+    std::vector<float> b(vols[g].bvals, vols[g].bvals + vols[g].n_meas);
+    std::sort(b.begin(), b.end());
+    int runs = 0;
+    for (size_t i = 0; i < b.size();) {
+      size_t j = i + 1;
+      while (j < b.size() && b[j] == b[i]) ++j;
+      if ((j - i) % 2 != 0) return false;
+      ++runs;
+      i = j;
+    }
+    if (runs > kMaxRuns) return false;
+  }
+  return true;
 }
 
 // Masked voxels of each volume.
@@ -1218,7 +1241,7 @@ extern "C" int prism_fit_init(const prism_volume* vols, int32_t n_vols, const pr
   int64_t V = 0;
   for (int64_t c : counts) V += c;
   int tpv = 1, nt = 128;
-  choose_shape(o, V, &tpv, &nt);
+  choose_shape(o, V, shells_apply(vols, n_vols, o), &tpv, &nt);
   if (o.autotune && o.fused) {
     int shells = o.shells;
     autotune_shape(vols, n_vols, counts, o, st, &tpv, &shells);
